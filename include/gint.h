@@ -1,0 +1,177 @@
+/*
+ * gint.h -- C ABI of the GB300 real-space grid integration library (libgint.so).
+ *
+ * The library evaluates the three-centre grid integrals of numerical-atomic-
+ * orbital DFT that the paper (arXiv 2409.09399, Section 2.2) identifies as the
+ * grid-integration hot path, on one NVIDIA GB300 (sm_103a):
+ *
+ *   H^V_IJ(T)[mu,nu] = sum_g sum_T1 phi_Imu(r_g - R_I - T1) V_g
+ *                                    phi_Jnu(r_g - R_J - T1 - T) dV      (Eq. 2)
+ *   rho_g            = sum over neighbour pairs ((I,T1),(J,T2)) of
+ *                      phi_Imu(r_g-R_I-T1) D_IJ(T2-T1)[mu,nu] phi_Jnu(r_g-R_J-T2)  (Eq. 3)
+ *   F_I              = -dE/dR_I at fixed V, E = sum_g V_g rho_g dV        (Eq. 4)
+ *   sigma            = -(1/Omega) dE/d(strain) at fixed V_g and dV        (Eq. 5)
+ *
+ * Conventions (all calls):
+ *   - Units: bohr and hartree.  Cell rows are the lattice vectors a1, a2, a3.
+ *   - Grid: r_g = sum_i (g_i/n_i) a_i, g_i in [0, n_i); dV = Omega/(n1 n2 n3).
+ *     Grid arrays (V, rho) are float64, C order [n1][n2][n3] (g3 fastest).
+ *   - Basis: phi = R_l(|d|) Y_lm(d/|d|) for |d| < rc of the atom's species,
+ *     R the cubic Hermite interpolant of the tabulated (y_k, y'_k) on knots
+ *     r_k = k*dr; Y_lm real, normalised, no Condon-Shortley phase, l <= 3.
+ *     Orbitals of an atom are ordered: l ascending, then radial functions in
+ *     the order given, then m = -l..l.
+ *   - Sparse matrices (H, D) live on the pair pattern: every block (I, J, T)
+ *     with |R_J + T - R_I| < rc_I + rc_J (Section 2.2: the pairs with
+ *     overlapping cutoff radii), sorted by (I, J, t1, t2, t3), T = sum t_i a_i.
+ *     Block b is row-major nw_I x nw_J float64 at offsets[b] (in elements).
+ *   - Device pointers are CUDA device (or managed) memory of the device the
+ *     handle was created on; the caller owns them.  The handle owns its
+ *     pattern, bricks, tables and scratch.
+ *   - Every compute call is asynchronous on the given stream (0 = legacy
+ *     default stream).  Arguments are validated on the host before anything is
+ *     enqueued; a failed call enqueues nothing and returns a status.  No call
+ *     traps or aborts.  Device-side anomalies raise a flag that gint_sync()
+ *     reports.
+ *   - A handle is not thread safe: calls on one handle must not overlap in
+ *     time on the host, and kernels from two calls on one handle must not run
+ *     concurrently on the device (they share the handle's scratch).
+ */
+#ifndef GINT_H
+#define GINT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gint_handle gint_handle;
+/* Same type as cudaStream_t; 0 is the legacy default stream. */
+typedef struct CUstream_st* gint_stream;
+
+typedef enum {
+    GINT_OK = 0,
+    GINT_ERR_INVALID_ARG = 1,      /* a null pointer, a size out of range, bad tables */
+    GINT_ERR_CUDA = 2,             /* a CUDA runtime call failed; see gint_last_error() */
+    GINT_ERR_OOM = 3,              /* device memory allocation failed */
+    GINT_ERR_PATTERN_MISMATCH = 4, /* a pair met on the grid is missing from the pattern */
+    GINT_ERR_TIMEOUT = 5,          /* a bounded device wait gave up */
+    GINT_ERR_UNSUPPORTED = 6,      /* a precision or basis this build does not implement */
+    GINT_ERR_DEVICE = 7            /* a device-side check failed; see gint_last_error() */
+} gint_status;
+
+/* Arithmetic of the per-batch work.  In every form the atom-to-brick offsets,
+ * the accumulation of batch results into H, rho, F and sigma, and the final
+ * reductions are FP64; the forms differ in the orbital values and the batch
+ * contractions.  GINT_FP64 is the plain FP64 form. */
+typedef enum {
+    GINT_FP64 = 0,
+    GINT_FP32 = 1,     /* FP32 orbital values and FP32 SIMT contractions */
+    GINT_TF32 = 2,     /* reserved */
+    GINT_BF16X3 = 3,   /* reserved */
+    GINT_BF16X6 = 4,   /* reserved */
+    GINT_FP16X3 = 5    /* reserved */
+} gint_precision;
+
+/* One tabulated radial function R(r): y[k] = R(k*dr), dy[k] = R'(k*dr),
+ * k = 0..n_knots-1.  Host pointers, read during gint_setup only. */
+typedef struct {
+    int l;              /* angular momentum, 0..3 */
+    int n_knots;        /* >= 2 */
+    double dr;          /* knot spacing (bohr), > 0; the same for all radials of a species */
+    const double* y;    /* n_knots values */
+    const double* dy;   /* n_knots derivatives (required) */
+} gint_radial;
+
+typedef struct {
+    double rc;                 /* cutoff radius (bohr); the table must cover [0, rc] */
+    int n_radial;              /* 1..16 */
+    const gint_radial* radial; /* n_radial entries; all with the same dr and n_knots */
+} gint_species;
+
+typedef struct {
+    int precision;   /* gint_precision */
+    int brick[3];    /* grid points per batch along a1, a2, a3; 0 = default (8, 8, 8).
+                        The product must be <= 2048. */
+    int device;      /* CUDA device ordinal; -1 = current device */
+    int reserved[5]; /* must be zero */
+} gint_options;
+
+/* Create a handle: uploads geometry and tables, builds the pair pattern
+ * (Section 2.2) and the batch/atom neighbour lists (Section 2.3.2) on the
+ * device.  Synchronous.
+ *   n_atoms  >= 1; pos[n_atoms][3] (host, bohr); species[n_atoms] (host) in [0, n_species);
+ *   cell[9] (host) rows a1, a2, a3 (bohr), right- or left-handed, non-singular;
+ *   sp[n_species] (host); grid[3] (host) each >= 1;
+ *   opt may be NULL for defaults; out receives the handle (NULL on failure). */
+gint_status gint_setup(int n_atoms, const double* pos, const int* species, const double* cell,
+                       int n_species, const gint_species* sp, const int* grid,
+                       const gint_options* opt, gint_handle** out);
+
+/* Release a handle and all device memory it owns.  NULL is a no-op. */
+void gint_destroy(gint_handle* h);
+
+/* The pair pattern.  *blocks points to device memory holding n_blocks rows of
+ * (I, J, t1, t2, t3) int32; *offsets to device memory holding n_blocks+1 int64
+ * element offsets (offsets[n_blocks] = n_values).  Both stay owned by the
+ * handle and valid until gint_destroy.  Any output pointer may be NULL. */
+gint_status gint_pattern(const gint_handle* h, int64_t* n_blocks, int64_t* n_values,
+                         const int32_t** blocks, const int64_t** offsets);
+
+/* Select the arithmetic of later calls (gint_precision). */
+gint_status gint_set_precision(gint_handle* h, int precision);
+
+/* H^V (Eq. 2).  V: device [n1][n2][n3] float64.  H: device, n_values float64
+ * on the pattern.  accumulate = 0 overwrites H; accumulate = 1 adds into the
+ * canonical blocks (I < J, or I == J and T >= 0 lexicographically) and then
+ * rewrites every other block as the transpose of its mirror, so H must be
+ * symmetric (H_JI(-T) = H_IJ(T)^T) on entry. */
+gint_status gint_vlocal(gint_handle* h, const double* V, double* H, int accumulate, gint_stream stream);
+
+/* rho (Eq. 3).  D: device, n_values float64 on the pattern; it must be
+ * symmetric (D_JI(-T) = D_IJ(T)^T): only the canonical blocks are read.
+ * rho: device [n1][n2][n3] float64, every element written. */
+gint_status gint_rho(gint_handle* h, const double* D, double* rho, gint_stream stream);
+
+/* Pulay force and stress (Eq. 4, 5) of E = sum_g V_g rho_g[D] dV at fixed V.
+ * V, D as above (D symmetric, canonical blocks read).  Outputs (device, float64,
+ * every non-NULL one overwritten):
+ *   F[n_atoms][3]            F_I = -dE/dR_I
+ *   sigma[3][3]              -(1/Omega) dE/d(eps_ab), eps a homogeneous strain
+ *                            applied to atoms, images and grid points alike
+ *   virial_atom[n_atoms][3][3]  per-atom parts Pi_I with sigma = -sum_I Pi_I / Omega
+ *   E[1]                     sum_g V_g rho_g dV
+ * At least one output must be non-NULL. */
+gint_status gint_force_stress(gint_handle* h, const double* V, const double* D, double* F,
+                              double* sigma, double* virial_atom, double* E, gint_stream stream);
+
+/* Wait for the handle's work on `stream` and report (then clear) any flag a
+ * device-side check raised since the last call. */
+gint_status gint_sync(gint_handle* h, gint_stream stream);
+
+/* Statistics of the handle's batches (for tests and benchmarks). */
+typedef struct {
+    int64_t n_blocks, n_values;   /* pattern size */
+    int64_t n_ext_atoms;          /* atom images whose cutoff sphere meets the grid */
+    int64_t n_bricks;             /* batches of grid points */
+    int64_t n_bricks_nonempty;    /* batches with at least one atom in range */
+    int64_t n_brick_atoms;        /* sum over batches of atoms in range */
+    int64_t n_brick_pairs;        /* sum over batches of atom pairs in the pattern */
+    int max_brick_atoms;          /* largest atom list of one batch */
+    int max_brick_orbitals;       /* largest orbital count of one batch */
+    int brick[3];
+    int precision;
+    int64_t scratch_bytes;        /* device scratch owned by the handle */
+} gint_info;
+
+gint_status gint_get_info(const gint_handle* h, gint_info* info);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* gint_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GINT_H */
