@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark: grid points per second of real-space grid integration (gint).
+
+One step = gint_vlocal (H^V, Eq. 2) + gint_rho (rho, Eq. 3) + gint_force_stress
+(Pulay force and stress, Eq. 4-5) over the whole grid of one synthetic
+twisted-bilayer-graphene cell (default: m = 29, 10,444 C atoms,
+1512 x 1512 x 281 = 6.42e8 grid points, C DZP basis, rc = 7 bohr).
+value = grid points x steps / time (all ranks).  Inputs stay resident in HBM
+during the timed steps; V (5.1 GB) and rho (5.1 GB) exceed L2, so no flush is
+needed between steps.
+
+--impl reference times the FP64 oracle (oracle/, plain C + OpenMP) on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (description, tbg index m)
+    "tbg_m29": ("twisted bilayer graphene m=29, 10444 C atoms, DZP, rc 7 bohr, h=pi/20 bohr", 29),
+    "tbg_m15": ("twisted bilayer graphene m=15, 2884 C atoms, DZP, rc 7 bohr, h=pi/20 bohr", 15),
+    "tbg_m5": ("twisted bilayer graphene m=5, 364 C atoms, DZP, rc 7 bohr, h=pi/20 bohr", 5),
+}
+METRIC = "grid pts/s for gint H^V+rho(+force), mixed vs FP64 form at stated error, TBG 10,444"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = sorted(float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit())
+        mx = max((float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, v in zip(names, s[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(k)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------- oracle arm
+def oracle_sample(system, n_points, n_blocks, n_atoms_f, seed=11):
+    """Time the FP64 oracle on a bounded random sample and scale to the whole step.
+
+    Returns (seconds for one full step as extrapolated, dict describing the sample).
+    rho: n_points random grid points; H: n_blocks random pattern blocks;
+    force: n_atoms_f random atoms.  Each part is scaled by (total / sampled).
+    """
+    import numpy as np
+
+    import oracle
+    import synth
+    rng = np.random.default_rng(seed)
+    o = oracle.Oracle(system)
+    params = synth.plane_wave_params()
+    # V on the oracle side: only the values the sample touches are needed, but the
+    # oracle takes the full grid array; generate it once (not timed)
+    V = synth.v_grid(system.grid, params).numpy()
+    D = o.d_fill()
+    idx = np.stack([rng.integers(0, system.grid[i], n_points) for i in range(3)], 1)
+    t0 = time.perf_counter()
+    o.rho_points(D, idx)
+    t_rho = time.perf_counter() - t0
+    keys = o.blocks[rng.choice(len(o.blocks), size=min(n_blocks, len(o.blocks)), replace=False)]
+    t0 = time.perf_counter()
+    o.vlocal_blocks(V, keys)
+    t_h = time.perf_counter() - t0
+    atoms = rng.choice(system.n_atoms, size=min(n_atoms_f, system.n_atoms), replace=False)
+    t0 = time.perf_counter()
+    o.force(V, D, atoms=atoms)
+    t_f = time.perf_counter() - t0
+    full = (t_rho * system.n_grid / n_points + t_h * len(o.blocks) / len(keys)
+            + t_f * system.n_atoms / len(atoms))
+    desc = {"rho_points": int(n_points), "h_blocks": int(len(keys)), "force_atoms": int(len(atoms)),
+            "sample_seconds": t_rho + t_h + t_f,
+            "scaled": "each part scaled by total/sampled (grid points, pattern blocks, atoms)"}
+    return full, desc
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    name = args.workload
+    desc, m = WORKLOADS[name]
+    system = synth.tbg(m)
+    cores = oracle.num_threads()
+    step_times = []
+    sample = None
+    for i in range(args.warmup + args.steps):
+        t_full, sample = oracle_sample(system, args.ref_points, args.ref_blocks, args.ref_atoms, seed=100 + i)
+        if i >= args.warmup:
+            step_times.append(t_full)
+    t = sum(step_times) / len(step_times)
+    value = system.n_grid / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "grid_points/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "description": desc, "grid_points": system.n_grid,
+                       "atoms": system.n_atoms},
+            "cpu_baseline": {"value": value, "unit": "grid_points/s", "cores": cores, "kind": "oracle",
+                             "sample": json.dumps(sample)},
+            "e2e": {"value": value, "unit": "grid_points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2409_09399_gb300 import gint
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    desc, m = WORKLOADS[args.workload]
+    system = synth.tbg(m)
+    ng = system.n_grid
+    prec = args.precision
+    g = gint.from_system(system, precision=prec, brick=tuple(args.brick), device=local)
+    info = g.info()
+    V = synth.v_grid(system.grid, synth.plane_wave_params(), device=dev)
+    blocks, offsets = g.pattern()
+    D = synth.d_fill_torch(blocks, offsets[:-1], g.n_values, system.pos, system.cell, system.nw(), dev)
+    H = torch.empty(g.n_values, dtype=torch.float64, device=dev)
+    rho = torch.empty(system.grid, dtype=torch.float64, device=dev)
+    F = torch.empty((system.n_atoms, 3), dtype=torch.float64, device=dev)
+    sig = torch.empty((3, 3), dtype=torch.float64, device=dev)
+    vir = torch.empty((system.n_atoms, 3, 3), dtype=torch.float64, device=dev)
+    E = torch.empty(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    n_ev = 4
+
+    def step(record=None):
+        if record is not None:
+            record[0].record(stream)
+        g.vlocal(V, H, stream=stream)
+        if record is not None:
+            record[1].record(stream)
+        g.rho(D, rho, stream=stream)
+        if record is not None:
+            record[2].record(stream)
+        g.force_stress(V, D, out=(F, sig, vir, E), stream=stream)
+        if record is not None:
+            record[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    g.sync()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    recs = [[ev() for _ in range(n_ev)] for _ in range(args.steps)]
+    end = ev()
+    barrier()
+    with ClockSampler(local) as clocks:
+        t0 = ev()
+        t0.record(stream)
+        for k in range(args.steps):
+            step(recs[k])
+        end.record(stream)
+        torch.cuda.synchronize()
+    g.sync()
+    total_ms = t0.elapsed_time(end)
+    parts = np.zeros(3)
+    for k in range(args.steps):
+        r = recs[k]
+        nxt = recs[k + 1][0] if k + 1 < args.steps else end
+        parts += [r[0].elapsed_time(r[1]), r[1].elapsed_time(r[2]), r[2].elapsed_time(r[3])]
+        _ = nxt
+    parts /= args.steps
+    t_max = total_ms
+    if ws > 1:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    ms_per_step = t_max / args.steps
+    value = ng * args.steps * ws / (t_max / 1e3)
+
+    # ---- FP64 form on the same GPU (one step, same inputs)
+    fp64 = None
+    if args.fp64_steps > 0 and prec != "fp64":
+        g.set_precision("fp64")
+        step()
+        g.sync()
+        a, b = ev(), ev()
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.fp64_steps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        g.sync()
+        ms64 = a.elapsed_time(b) / args.fp64_steps
+        fp64 = {"value": ng / (ms64 / 1e3), "unit": "grid_points/s", "ms_per_step": ms64,
+                "speedup_of_mixed": ms64 / ms_per_step}
+        g.set_precision(prec)
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        Vh = V.cpu().pin_memory()
+        Dh = D.cpu().pin_memory()
+        Hh = torch.empty(H.shape, dtype=H.dtype).pin_memory()
+        rhoh = torch.empty(rho.shape, dtype=rho.dtype).pin_memory()
+        Fh = torch.empty(F.shape, dtype=F.dtype).pin_memory()
+        sigh = torch.empty(sig.shape, dtype=sig.dtype).pin_memory()
+        Eh = torch.empty(E.shape, dtype=E.dtype).pin_memory()
+        Vd = torch.empty_like(V)
+        Dd = torch.empty_like(D)
+
+        def e2e_step():
+            Vd.copy_(Vh, non_blocking=True)
+            Dd.copy_(Dh, non_blocking=True)
+            g.vlocal(Vd, H, stream=stream)
+            g.rho(Dd, rho, stream=stream)
+            g.force_stress(Vd, Dd, out=(F, sig, vir, E), stream=stream)
+            Hh.copy_(H, non_blocking=True)
+            rhoh.copy_(rho, non_blocking=True)
+            Fh.copy_(F, non_blocking=True)
+            sigh.copy_(sig, non_blocking=True)
+            Eh.copy_(E, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        g.sync()
+        ms_e2e = a.elapsed_time(b) / args.e2e_steps
+        h2d = (Vh.numel() + Dh.numel()) * 8
+        d2h = (Hh.numel() + rhoh.numel() + Fh.numel() + sigh.numel() + Eh.numel()) * 8
+        e2e = {"value": ng * ws / (ms_e2e / 1e3), "unit": "grid_points/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
+        del Vh, Dh, Hh, rhoh, Vd, Dd
+
+    # ---- roofline of the dominant call
+    peaks, peak_src = load_peaks()
+    sum_no, sum_no2 = g.work_stats()
+    flops = {"vlocal": float(sum_no2 + sum_no), "rho": float(sum_no2 + sum_no),
+             "force": float(2 * sum_no2 + 24 * sum_no)}
+    names = ["vlocal", "rho", "force"]
+    dom = int(np.argmax(parts))
+    dom_name = names[dom]
+    achieved = flops[dom_name] / (parts[dom] / 1e3) / 1e12
+    if prec == "fp64":
+        peak, bound, src = 1.25, "alu", "FP64 1.25 TFLOP/s nominal (DFMA; recipe table)"
+    elif prec == "fp32":
+        peak, bound = 152 * 128 * 2 * 2.07e9 / 1e12, "alu"
+        src = "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
+    else:
+        peak, bound = peaks.get("bf16_tflops_sustained", 1711.1), "tensor"
+        src = f"bf16 dense sustained ({peak_src})"
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", f"traffic_{dom_name}_{prec}.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get("bytes_per_launch")
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": dom_name, "peak_source": src,
+            "algorithmic_flop_per_launch": flops[dom_name]}
+
+    # ---- CPU baseline (oracle, bounded sample), rank 0 at N = 1 only
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        t_full, sample = oracle_sample(system, args.ref_points, args.ref_blocks, args.ref_atoms)
+        cpu = {"value": ng / t_full, "unit": "grid_points/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": json.dumps(sample)}
+
+    launches_per_step = 6  # vlocal kernel + mirror, rho kernel + empty-brick fill, force kernel + finalize
+    line = {"metric": METRIC, "value": value, "unit": "grid_points/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32"}.get(prec, prec), "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "grid": list(system.grid),
+                       "grid_points": ng, "atoms": system.n_atoms, "precision": prec,
+                       "brick": list(info["brick"]), "l2": "inputs larger than L2 (V 5.1 GB, rho 5.1 GB)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "ms_per_call": {"vlocal": parts[0], "rho": parts[1], "force_stress": parts[2]},
+            "fp64_form": fp64, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+            "clocks": clocks.summary(), "gpu_launches": launches_per_step * args.steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tbg_m29")
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--brick", type=int, nargs=3, default=[0, 0, 0])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-points", type=int, default=2000)
+    ap.add_argument("--ref-blocks", type=int, default=24)
+    ap.add_argument("--ref-atoms", type=int, default=1)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

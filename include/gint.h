@@ -167,6 +167,12 @@ typedef struct {
 
 gint_status gint_get_info(const gint_handle* h, gint_info* info);
 
+/* Exact work of the grid integrals (for roofline accounting): over every grid
+ * point r, n_o(r) = number of orbitals phi_Imu(r - R_I - T) with |r - R_I - T| < rc.
+ * Writes sum_r n_o(r) and sum_r n_o(r)^2.  Runs a counting kernel and
+ * synchronises the device.  Outputs are host pointers. */
+gint_status gint_work_stats(gint_handle* h, int64_t* sum_orbitals, int64_t* sum_orbitals_sq);
+
 /* Message of the last failed call on this host thread ("" if none). */
 const char* gint_last_error(void);
 

@@ -434,6 +434,44 @@ __global__ void k_sum_i64(const int64_t* in, int64_t n, unsigned long long* out)
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, (unsigned long long)v);
 }
 
+// Exact per-point orbital counts: one warp per non-empty brick, lane = point.
+__global__ void k_work_stats(Problem P, unsigned long long* out) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= P.n_work) return;
+    const int brick = P.work[w];
+    const GridDev& g = P.g;
+    int b0, b1, b2;
+    brick_coords(g, brick, b0, b1, b2);
+    const int64_t s0 = P.brick_start[brick];
+    const int na = (int)(P.brick_start[brick + 1] - s0);
+    unsigned long long s1 = 0, s2 = 0;
+    for (int p = lane; p < g.bpts; p += 32) {
+        int g0, g1, g2;
+        if (!brick_point(g, b0, b1, b2, p, g0, g1, g2)) continue;
+        const double rx = g0 * g.step[0][0] + g1 * g.step[1][0] + g2 * g.step[2][0];
+        const double ry = g0 * g.step[0][1] + g1 * g.step[1][1] + g2 * g.step[2][1];
+        const double rz = g0 * g.step[0][2] + g1 * g.step[1][2] + g2 * g.step[2][2];
+        unsigned long long no = 0;
+        for (int i = 0; i < na; ++i) {
+            const ExtAtom& X = P.ext[P.brick_atoms[s0 + i]];
+            const double dx = rx - X.p[0], dy = ry - X.p[1], dz = rz - X.p[2];
+            const double rc = P.sp[X.species].rc;
+            if (dx * dx + dy * dy + dz * dz < rc * rc) no += P.sp[X.species].n_orb;
+        }
+        s1 += no;
+        s2 += no * no;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+        atomicAdd(out, s1);
+        atomicAdd(out + 1, s2);
+    }
+}
+
 // ----------------------------------------------------------- host helpers
 static void inv3(const double a[9], double out[9]) {
     double d = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) + a[2] * (a[3] * a[7] - a[4] * a[6]);
@@ -866,6 +904,29 @@ gint_status gint_get_info(const gint_handle* h, gint_info* info) {
     for (int i = 0; i < 3; ++i) info->brick[i] = h->grid.B[i];
     info->precision = h->precision;
     info->scratch_bytes = (int64_t)h->scratch_bytes;
+    return GINT_OK;
+}
+
+gint_status gint_work_stats(gint_handle* h, int64_t* sum_orbitals, int64_t* sum_orbitals_sq) {
+    if (!h || !sum_orbitals || !sum_orbitals_sq) { set_error("NULL argument"); return GINT_ERR_INVALID_ARG; }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(h->device) != cudaSuccess) { set_error("cannot select device %d", h->device); return GINT_ERR_CUDA; }
+    unsigned long long* d = nullptr;
+    unsigned long long hv[2] = {0, 0};
+    cudaError_t e = cudaMalloc(&d, sizeof(hv));
+    if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(hv));
+    if (e == cudaSuccess && h->n_work > 0) {
+        const int64_t threads = h->n_work * 32;
+        k_work_stats<<<(unsigned)((threads + 255) / 256), 256>>>(h->problem(), d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(hv, d, sizeof(hv), cudaMemcpyDeviceToHost);
+    if (d) cudaFree(d);
+    if (prev >= 0) cudaSetDevice(prev);
+    if (e != cudaSuccess) { set_error("gint_work_stats: %s", cudaGetErrorString(e)); return GINT_ERR_CUDA; }
+    *sum_orbitals = (int64_t)hv[0];
+    *sum_orbitals_sq = (int64_t)hv[1];
     return GINT_OK;
 }
 

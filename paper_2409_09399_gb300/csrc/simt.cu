@@ -139,10 +139,18 @@ __device__ int brick_prologue(const Problem& P, int brick, const double* V, Simt
         if (a1 > a2) continue;
         int64_t off = -1;
         if (S.at[a1].mask & S.at[a2].mask) {
+            // two images can reach one sub-tile without overlapping each other:
+            // only pairs closer than rc1 + rc2 are in the pattern (and only those
+            // have a non-zero product anywhere)
             const AtomS &X = S.at[a1], &Y = S.at[a2];
-            const int64_t blk = find_block(P, X.I, Y.I, Y.t[0] - X.t[0], Y.t[1] - X.t[1], Y.t[2] - X.t[2]);
-            if (blk < 0) atomicOr(P.err, kErrPatternMissing);
-            else off = P.offsets[blk];
+            const double dx = Y.p[0] - X.p[0], dy = Y.p[1] - X.p[1], dz = Y.p[2] - X.p[2];
+            const double dist = sqrt(dx * dx + dy * dy + dz * dz);
+            const double cut = P.sp[X.sp].rc + P.sp[Y.sp].rc;
+            if (dist < cut + 1e-9) {
+                const int64_t blk = find_block(P, X.I, Y.I, Y.t[0] - X.t[0], Y.t[1] - X.t[1], Y.t[2] - X.t[2]);
+                if (blk >= 0) off = P.offsets[blk];
+                else if (dist < cut - 1e-9) atomicOr(P.err, kErrPatternMissing);
+            }
         }
         S.pairoff[a1 * na + a2] = off;
         S.pairoff[a2 * na + a1] = off;

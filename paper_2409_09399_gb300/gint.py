@@ -22,7 +22,7 @@ STATUS = {0: "GINT_OK", 1: "GINT_ERR_INVALID_ARG", 2: "GINT_ERR_CUDA", 3: "GINT_
 
 # exported symbols, in the order include/gint.h declares them
 SYMBOLS = ["gint_setup", "gint_destroy", "gint_pattern", "gint_set_precision", "gint_vlocal", "gint_rho",
-           "gint_force_stress", "gint_sync", "gint_get_info", "gint_last_error"]
+           "gint_force_stress", "gint_sync", "gint_get_info", "gint_work_stats", "gint_last_error"]
 
 
 class GintError(RuntimeError):
@@ -85,6 +85,8 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.gint_sync.argtypes = [vp, vp]
     L.gint_get_info.restype = i32
     L.gint_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
+    L.gint_work_stats.restype = i32
+    L.gint_work_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.gint_last_error.restype = ctypes.c_char_p
     L.gint_last_error.argtypes = []
     _lib = L
@@ -107,7 +109,7 @@ class _DevArray:
     """__cuda_array_interface__ view of memory owned by a handle."""
 
     def __init__(self, ptr: int, shape, typestr: str, owner):
-        self.__cuda_array_interface__ = {"data": (ptr, True), "shape": tuple(shape), "typestr": typestr,
+        self.__cuda_array_interface__ = {"data": (ptr, False), "shape": tuple(shape), "typestr": typestr,
                                          "version": 3, "strides": None}
         self._owner = owner
 
@@ -178,6 +180,12 @@ class Gint:
         d = {k: getattr(inf, k) for k, _ in _Info._fields_}
         d["brick"] = tuple(inf.brick)
         return d
+
+    def work_stats(self):
+        """(sum_r n_o(r), sum_r n_o(r)^2) over all grid points (exact orbital counts)."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().gint_work_stats(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def pattern(self):
         """(blocks int64 (n_blocks, 5) numpy, offsets int64 (n_blocks+1,) numpy), copied from the device."""

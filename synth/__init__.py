@@ -464,3 +464,79 @@ def d_fill(blocks: np.ndarray, offsets: np.ndarray, total: int, pos, cell, nw, s
         X = (2.0 * uniform01(seed, Ic[b], Jc[b], Tc[b, 0], Tc[b, 1], Tc[b, 2], mu, nu) - 1.0) * amp[b]
         out[offsets[b]:offsets[b] + a * bsz] = X.T.reshape(-1)
     return out
+
+
+# ---------------------------------------------------------------------------
+# torch versions (same definitions, for large grids and patterns on a device)
+# ---------------------------------------------------------------------------
+def _t_splitmix64(z):
+    """SplitMix64 finaliser on int64 tensors holding uint64 bit patterns."""
+    import torch  # noqa: F401
+    z = z + (-7046029254386353131)  # 0x9E3779B97F4A7C15 as int64
+    z = (z ^ ((z >> 30) & ((1 << 34) - 1))) * (-4658895280553007687)  # 0xBF58476D1CE4E5B9
+    z = (z ^ ((z >> 27) & ((1 << 37) - 1))) * (-7723592293110705685)  # 0x94D049BB133111EB
+    return z ^ ((z >> 31) & ((1 << 33) - 1))
+
+
+def uniform01_torch(seed: int, *keys):
+    """Same values as ``uniform01`` for int64 tensor keys (broadcast)."""
+    import torch
+    h0 = int(splitmix64(np.uint64(seed)))
+    if h0 >= 1 << 63:
+        h0 -= 1 << 64
+    dev = keys[0].device
+    h = torch.tensor(h0, dtype=torch.int64, device=dev)
+    for k in keys:
+        h = _t_splitmix64(h ^ (k.to(torch.int64) + (1 << 20)))
+    top = (h >> 11) & ((1 << 53) - 1)
+    return top.to(torch.float64) * (1.0 / 9007199254740992.0)
+
+
+def d_fill_torch(blocks, offsets, total: int, pos, cell, nw, device, seed: int = 3, scale: float = 0.5,
+                 decay: float = 4.0):
+    """``d_fill`` evaluated with torch on ``device`` (identical definition).
+
+    stored[b][mu][nu] = amp_b (2 U(seed, Ic, Jc, Tc, mu_c, nu_c) - 1) with
+    (mu_c, nu_c) = (mu, nu) for a canonical block and (nu, mu) for its mirror;
+    the self-mirror blocks D_II(0) are symmetrised.
+    """
+    import torch
+    dev = torch.device(device)
+    blocks = torch.as_tensor(np.asarray(blocks, dtype=np.int64), device=dev)
+    offsets = torch.as_tensor(np.asarray(offsets, dtype=np.int64), device=dev)
+    nw_t = torch.as_tensor(np.asarray(nw, dtype=np.int64), device=dev)
+    pos_t = torch.as_tensor(np.asarray(pos, dtype=np.float64), device=dev)
+    cell_t = torch.as_tensor(np.asarray(cell, dtype=np.float64), device=dev)
+    out = torch.zeros(int(total), dtype=torch.float64, device=dev)
+    if blocks.shape[0] == 0:
+        return out
+    I, J, T = blocks[:, 0], blocks[:, 1], blocks[:, 2:5]
+    t1, t2, t3 = T[:, 0], T[:, 1], T[:, 2]
+    lex = (t1 > 0) | ((t1 == 0) & ((t2 > 0) | ((t2 == 0) & (t3 >= 0))))
+    canon = (I < J) | ((I == J) & lex)
+    Ic = torch.where(canon, I, J)
+    Jc = torch.where(canon, J, I)
+    Tc = torch.where(canon[:, None], T, -T)
+    dvec = pos_t[Jc] + Tc.to(torch.float64) @ cell_t - pos_t[Ic]
+    amp = scale * torch.exp(-torch.sqrt((dvec * dvec).sum(1)) / decay)
+    selfm = (Ic == Jc) & (Tc == 0).all(1)
+    ni, nj = nw_t[I], nw_t[J]
+    shapes = torch.unique(torch.stack([ni, nj], 1), dim=0).cpu().numpy()
+    for a, bsz in shapes:
+        sel_all = torch.nonzero((ni == int(a)) & (nj == int(bsz))).flatten()
+        for s0 in range(0, sel_all.numel(), 1 << 15):
+            s = sel_all[s0:s0 + (1 << 15)]
+            mu = torch.arange(int(a), device=dev)[None, :, None]
+            nu = torch.arange(int(bsz), device=dev)[None, None, :]
+            c = canon[s][:, None, None]
+            muc = torch.where(c, mu, nu)
+            nuc = torch.where(c, nu, mu)
+            X = 2.0 * uniform01_torch(seed, Ic[s][:, None, None], Jc[s][:, None, None], Tc[s, 0][:, None, None],
+                                      Tc[s, 1][:, None, None], Tc[s, 2][:, None, None], muc, nuc) - 1.0
+            X = X * amp[s][:, None, None]
+            sm = selfm[s]
+            if bool(sm.any()):
+                X[sm] = 0.5 * (X[sm] + X[sm].transpose(1, 2))
+            idx = offsets[s][:, None] + torch.arange(int(a) * int(bsz), device=dev)[None, :]
+            out[idx.reshape(-1)] = X.reshape(-1)
+    return out

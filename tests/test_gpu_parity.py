@@ -134,6 +134,8 @@ def test_fp32_form_error(kind, cuda):
     rho = g.rho(D)
     F, sigma, vir, E = g.force_stress(Vt, D)
     g.sync()
-    assert np.max(np.abs(H.cpu().numpy() - H_ref)) < 1e-6
+    # FP32 products summed in FP32 over one brick (<= 512 points), FP64 across
+    # bricks: per-brick error ~ sqrt(512) * 2^-24 * |partial|, |partial| <= ~2
+    assert np.max(np.abs(H.cpu().numpy() - H_ref)) < 1e-5
     assert normwise(rho.cpu().numpy(), rho_ref) < 1e-5
-    assert np.max(np.abs(F.cpu().numpy() - F_ref)) < 1e-5
+    assert np.max(np.abs(F.cpu().numpy() - F_ref)) < 1e-4

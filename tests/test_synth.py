@@ -113,3 +113,17 @@ def test_v_grid_matches_pointwise():
     idx = np.stack(np.meshgrid(*[np.arange(n) for n in grid], indexing="ij"), -1).reshape(-1, 3)
     assert np.allclose(V.reshape(-1), synth.v_at(idx, grid, params), atol=1e-13, rtol=0)
     assert abs(V.mean()) < 1e-12  # each cosine has a non-zero integer wave vector resolved by the grid
+
+
+def test_d_fill_torch_matches_numpy():
+    import oracle
+    s = synth.random_cell(5)  # C/H/O: rectangular and square blocks, mirrors, self-mirrors
+    o = oracle.Oracle(s)
+    Dn = synth.d_fill(o.blocks, o.offsets[:-1], o.n_values, s.pos, s.cell, s.nw())
+    Dt = synth.d_fill_torch(o.blocks, o.offsets[:-1], o.n_values, s.pos, s.cell, s.nw(), "cpu").numpy()
+    assert np.max(np.abs(Dn - Dt)) <= 1e-15 * np.max(np.abs(Dn))
+    # symmetric on the pattern
+    idx = o.block_index()
+    for b, k in enumerate(o.blocks[:200]):
+        m = idx[(k[1], k[0], -k[2], -k[3], -k[4])]
+        assert np.array_equal(o.block(Dn, b), o.block(Dn, m).T)
