@@ -69,9 +69,10 @@ typedef enum {
     GINT_FP64 = 0,
     GINT_FP32 = 1,     /* FP32 orbital values and FP32 SIMT contractions */
     GINT_TF32 = 2,     /* reserved */
-    GINT_BF16X3 = 3,   /* reserved */
+    GINT_BF16X3 = 3,   /* H^V on the tensor cores: operands split x = hi + lo in bf16,
+                          products hi*hi + hi*lo + lo*hi, FP32 accumulation per brick */
     GINT_BF16X6 = 4,   /* reserved */
-    GINT_FP16X3 = 5    /* reserved */
+    GINT_FP16X3 = 5    /* as GINT_BF16X3 with fp16 pieces (22-bit products) */
 } gint_precision;
 
 /* One tabulated radial function R(r): y[k] = R(k*dr), dy[k] = R'(k*dr),

@@ -11,6 +11,7 @@ gint_status launch_mirror(gint_handle* h, double* H, cudaStream_t st);
 gint_status launch_rho_empty(gint_handle* h, double* rho, cudaStream_t st);
 gint_status launch_force_finalize(gint_handle* h, double* F, double* sigma, double* virial, double* E,
                                   cudaStream_t st);
+gint_status tc_vlocal(gint_handle* h, int bf16, const double* V, double* H, cudaStream_t st);
 
 namespace {
 // Selects the handle's device for the duration of a call.
@@ -26,9 +27,15 @@ struct DeviceGuard {
     }
 };
 
+// FP64: SIMT FP64.  FP32: SIMT FP32.  BF16X3 / FP16X3: H^V on the tensor
+// cores (split 16-bit operands, three products, FP32 accumulation); rho and
+// force in the FP32 SIMT kernels.
 gint_status check_precision(const gint_handle* h, bool* fp32) {
     if (h->precision == GINT_FP64) { *fp32 = false; return GINT_OK; }
-    if (h->precision == GINT_FP32) { *fp32 = true; return GINT_OK; }
+    if (h->precision == GINT_FP32 || h->precision == GINT_BF16X3 || h->precision == GINT_FP16X3) {
+        *fp32 = true;
+        return GINT_OK;
+    }
     set_error("precision %d is not implemented by this build", h->precision);
     return GINT_ERR_UNSUPPORTED;
 }
@@ -50,7 +57,10 @@ gint_status gint_vlocal(gint_handle* h, const double* V, double* H, int accumula
     if (!dg.ok) { set_error("cannot select device %d", h->device); return GINT_ERR_CUDA; }
     cudaStream_t st = (cudaStream_t)stream;
     if (!accumulate && h->n_values > 0) GINT_CUDA_TRY(cudaMemsetAsync(H, 0, sizeof(double) * h->n_values, st));
-    s = simt_run(h, 0, fp32, V, nullptr, H, nullptr, nullptr, st);
+    if (h->precision == GINT_BF16X3 || h->precision == GINT_FP16X3)
+        s = tc_vlocal(h, h->precision == GINT_BF16X3 ? 1 : 0, V, H, st);
+    else
+        s = simt_run(h, 0, fp32, V, nullptr, H, nullptr, nullptr, st);
     if (s != GINT_OK) return s;
     return launch_mirror(h, H, st);
 }

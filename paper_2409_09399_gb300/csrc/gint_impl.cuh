@@ -85,6 +85,7 @@ struct Problem {
 enum : int {
     kErrPatternMissing = 1,
     kErrBrickTooLarge = 2,
+    kErrTimeout = 4,  // a bounded wait on the tensor-core pipeline gave up
 };
 
 }  // namespace gint

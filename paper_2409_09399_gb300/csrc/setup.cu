@@ -942,6 +942,7 @@ gint_status gint_sync(gint_handle* h, gint_stream stream) {
     if (prev >= 0) cudaSetDevice(prev);
     if (e != cudaSuccess) { set_error("gint_sync: %s", cudaGetErrorString(e)); return GINT_ERR_CUDA; }
     if (flags & kErrPatternMissing) { set_error("a pair of atoms met on the grid is missing from the pattern"); return GINT_ERR_PATTERN_MISMATCH; }
+    if (flags & kErrTimeout) { set_error("a bounded wait on the tensor-core pipeline gave up"); return GINT_ERR_TIMEOUT; }
     if (flags) { set_error("device check failed (flags 0x%x)", flags); return GINT_ERR_DEVICE; }
     return GINT_OK;
 }
