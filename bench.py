@@ -103,9 +103,10 @@ def dist_env():
 def oracle_sample(system, n_points, n_blocks, n_atoms_f, seed=11):
     """Time the FP64 oracle on a bounded random sample and scale to the whole step.
 
-    Returns (seconds for one full step as extrapolated, dict describing the sample).
-    rho: n_points random grid points; H: n_blocks random pattern blocks;
-    force: n_atoms_f random atoms.  Each part is scaled by (total / sampled).
+    Returns (seconds for one full step as extrapolated, description, sampled
+    oracle outputs).  rho: n_points random grid points (uniform over the grid, so
+    vacuum included); H: n_blocks random pattern blocks; force: n_atoms_f random
+    atoms.  Each part is scaled by (total / sampled).
     """
     import numpy as np
 
@@ -114,28 +115,45 @@ def oracle_sample(system, n_points, n_blocks, n_atoms_f, seed=11):
     rng = np.random.default_rng(seed)
     o = oracle.Oracle(system)
     params = synth.plane_wave_params()
-    # V on the oracle side: only the values the sample touches are needed, but the
-    # oracle takes the full grid array; generate it once (not timed)
-    V = synth.v_grid(system.grid, params).numpy()
+    V = synth.v_grid(system.grid, params).numpy()  # input generation, not timed
     D = o.d_fill()
     idx = np.stack([rng.integers(0, system.grid[i], n_points) for i in range(3)], 1)
     t0 = time.perf_counter()
-    o.rho_points(D, idx)
+    rho_s = o.rho_points(D, idx)
     t_rho = time.perf_counter() - t0
-    keys = o.blocks[rng.choice(len(o.blocks), size=min(n_blocks, len(o.blocks)), replace=False)]
+    bsel = rng.choice(len(o.blocks), size=min(n_blocks, len(o.blocks)), replace=False)
+    keys = o.blocks[bsel]
     t0 = time.perf_counter()
-    o.vlocal_blocks(V, keys)
+    H_s = o.vlocal_blocks(V, keys)
     t_h = time.perf_counter() - t0
     atoms = rng.choice(system.n_atoms, size=min(n_atoms_f, system.n_atoms), replace=False)
     t0 = time.perf_counter()
-    o.force(V, D, atoms=atoms)
+    F_s, _ = o.force(V, D, atoms=atoms)
     t_f = time.perf_counter() - t0
     full = (t_rho * system.n_grid / n_points + t_h * len(o.blocks) / len(keys)
             + t_f * system.n_atoms / len(atoms))
     desc = {"rho_points": int(n_points), "h_blocks": int(len(keys)), "force_atoms": int(len(atoms)),
             "sample_seconds": t_rho + t_h + t_f,
             "scaled": "each part scaled by total/sampled (grid points, pattern blocks, atoms)"}
-    return full, desc
+    samples = {"idx": idx, "rho": rho_s, "blocks": bsel, "H": H_s, "atoms": atoms, "F": F_s,
+               "oracle_blocks": o.blocks}
+    return full, desc, samples
+
+
+def sample_errors(samples, H, rho, F, blocks, offsets):
+    """Errors of GPU results against the oracle's sampled outputs (same pattern order)."""
+    import numpy as np
+    if not np.array_equal(blocks, samples["oracle_blocks"]):
+        return {"error": "pattern differs from the oracle's"}
+    Hn = H.cpu().numpy()
+    eh = 0.0
+    for b, ref in zip(samples["blocks"], samples["H"]):
+        eh = max(eh, float(np.max(np.abs(Hn[offsets[b]:offsets[b + 1]].reshape(ref.shape) - ref))))
+    idx = samples["idx"]
+    rho_g = rho[idx[:, 0], idx[:, 1], idx[:, 2]].cpu().numpy()
+    er = float(np.max(np.abs(rho_g - samples["rho"])) / max(1e-300, np.max(np.abs(samples["rho"]))))
+    ef = float(np.max(np.abs(F.cpu().numpy()[samples["atoms"]] - samples["F"])))
+    return {"H_abs": eh, "rho_rel": er, "F_abs": ef, "gates": {"H_abs": 1e-7, "rho_rel": 1e-6, "F_abs": 1e-5}}
 
 
 def run_reference(args):
@@ -151,7 +169,7 @@ def run_reference(args):
     step_times = []
     sample = None
     for i in range(args.warmup + args.steps):
-        t_full, sample = oracle_sample(system, args.ref_points, args.ref_blocks, args.ref_atoms, seed=100 + i)
+        t_full, sample, _ = oracle_sample(system, args.ref_points, args.ref_blocks, args.ref_atoms, seed=100 + i)
         if i >= args.warmup:
             step_times.append(t_full)
     t = sum(step_times) / len(step_times)
@@ -251,6 +269,8 @@ def run_ours(args):
     ms_per_step = t_max / args.steps
     value = ng * args.steps * ws / (t_max / 1e3)
 
+    H_mixed, rho_mixed, F_mixed = H.clone(), rho.clone(), F.clone()
+
     # ---- FP64 form on the same GPU (one step, same inputs)
     fp64 = None
     if args.fp64_steps > 0 and prec != "fp64":
@@ -268,6 +288,7 @@ def run_ours(args):
         ms64 = a.elapsed_time(b) / args.fp64_steps
         fp64 = {"value": ng / (ms64 / 1e3), "unit": "grid_points/s", "ms_per_step": ms64,
                 "speedup_of_mixed": ms64 / ms_per_step}
+        H_fp64, rho_fp64, F_fp64 = H.clone(), rho.clone(), F.clone()
         g.set_precision(prec)
 
     # ---- end to end through the public API with host buffers
@@ -327,8 +348,9 @@ def run_ours(args):
         peak, bound = 152 * 128 * 2 * 2.07e9 / 1e12, "alu"
         src = "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
     else:
+        # fp16 and bf16 share the dense 16-bit tensor rate
         peak, bound = peaks.get("bf16_tflops_sustained", 1711.1), "tensor"
-        src = f"bf16 dense sustained ({peak_src})"
+        src = f"16-bit dense tensor, sustained ({peak_src} bf16 cuBLAS loop)"
     traffic = None
     tpath = os.path.join(ROOT, "profiles", f"traffic_{dom_name}_{prec}.json")
     if os.path.exists(tpath):
@@ -340,22 +362,29 @@ def run_ours(args):
 
     # ---- CPU baseline (oracle, bounded sample), rank 0 at N = 1 only
     cpu = None
+    errors = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
-        t_full, sample = oracle_sample(system, args.ref_points, args.ref_blocks, args.ref_atoms)
+        t_full, sample, samples = oracle_sample(system, args.ref_points, args.ref_blocks, args.ref_atoms)
         cpu = {"value": ng / t_full, "unit": "grid_points/s", "cores": oracle.num_threads(), "kind": "oracle",
                "sample": json.dumps(sample)}
+        errors = {prec: sample_errors(samples, H_mixed, rho_mixed, F_mixed, blocks, offsets)}
+        if fp64 is not None:
+            errors["fp64"] = sample_errors(samples, H_fp64, rho_fp64, F_fp64, blocks, offsets)
+        errors["sample"] = "oracle outputs at the cpu_baseline sample (random points, blocks, atoms)"
 
-    launches_per_step = 6  # vlocal kernel + mirror, rho kernel + empty-brick fill, force kernel + finalize
+    # vlocal kernel + mirror; rho (+ D format on the tensor path) + empty-brick fill; force (+ D format) + finalize
+    launches_per_step = 6 if prec in ("fp64", "fp32") else 8
     line = {"metric": METRIC, "value": value, "unit": "grid_points/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32"}.get(prec, prec), "data": "synthetic",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16x3": "f16x3", "bf16x3": "bf16x3"}.get(prec, prec),
+            "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "grid": list(system.grid),
                        "grid_points": ng, "atoms": system.n_atoms, "precision": prec,
                        "brick": list(info["brick"]), "l2": "inputs larger than L2 (V 5.1 GB, rho 5.1 GB)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "ms_per_call": {"vlocal": parts[0], "rho": parts[1], "force_stress": parts[2]},
-            "fp64_form": fp64, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+            "fp64_form": fp64, "errors_vs_oracle": errors, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
             "clocks": clocks.summary(), "gpu_launches": launches_per_step * args.steps}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -371,7 +400,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tbg_m29")
-    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--precision", default="fp16x3")
     ap.add_argument("--brick", type=int, nargs=3, default=[0, 0, 0])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)

@@ -12,6 +12,8 @@ gint_status launch_rho_empty(gint_handle* h, double* rho, cudaStream_t st);
 gint_status launch_force_finalize(gint_handle* h, double* F, double* sigma, double* virial, double* E,
                                   cudaStream_t st);
 gint_status tc_vlocal(gint_handle* h, int bf16, const double* V, double* H, cudaStream_t st);
+gint_status tc_rhoforce(gint_handle* h, int bf16, bool force, const double* V, const double* D, double* rho,
+                        double* facc, double* acc_e, cudaStream_t st);
 
 namespace {
 // Selects the handle's device for the duration of a call.
@@ -27,9 +29,8 @@ struct DeviceGuard {
     }
 };
 
-// FP64: SIMT FP64.  FP32: SIMT FP32.  BF16X3 / FP16X3: H^V on the tensor
-// cores (split 16-bit operands, three products, FP32 accumulation); rho and
-// force in the FP32 SIMT kernels.
+// FP64: SIMT FP64.  FP32: SIMT FP32.  BF16X3 / FP16X3: tensor cores (split
+// 16-bit operands, three products, FP32 accumulation per brick).
 gint_status check_precision(const gint_handle* h, bool* fp32) {
     if (h->precision == GINT_FP64) { *fp32 = false; return GINT_OK; }
     if (h->precision == GINT_FP32 || h->precision == GINT_BF16X3 || h->precision == GINT_FP16X3) {
@@ -74,7 +75,10 @@ gint_status gint_rho(gint_handle* h, const double* D, double* rho, gint_stream s
     DeviceGuard dg(h->device);
     if (!dg.ok) { set_error("cannot select device %d", h->device); return GINT_ERR_CUDA; }
     cudaStream_t st = (cudaStream_t)stream;
-    s = simt_run(h, 1, fp32, nullptr, D, rho, nullptr, nullptr, st);
+    if (h->precision == GINT_BF16X3 || h->precision == GINT_FP16X3)
+        s = tc_rhoforce(h, h->precision == GINT_BF16X3 ? 1 : 0, false, nullptr, D, rho, nullptr, nullptr, st);
+    else
+        s = simt_run(h, 1, fp32, nullptr, D, rho, nullptr, nullptr, st);
     if (s != GINT_OK) return s;
     return launch_rho_empty(h, rho, st);
 }
@@ -92,7 +96,10 @@ gint_status gint_force_stress(gint_handle* h, const double* V, const double* D, 
     cudaStream_t st = (cudaStream_t)stream;
     GINT_CUDA_TRY(cudaMemsetAsync(h->d_facc, 0, sizeof(double) * 12 * h->n_atoms, st));
     GINT_CUDA_TRY(cudaMemsetAsync(h->d_red, 0, sizeof(double), st));
-    s = simt_run(h, 2, fp32, V, D, nullptr, h->d_facc, h->d_red, st);
+    if (h->precision == GINT_BF16X3 || h->precision == GINT_FP16X3)
+        s = tc_rhoforce(h, h->precision == GINT_BF16X3 ? 1 : 0, true, V, D, nullptr, h->d_facc, h->d_red, st);
+    else
+        s = simt_run(h, 2, fp32, V, D, nullptr, h->d_facc, h->d_red, st);
     if (s != GINT_OK) return s;
     return launch_force_finalize(h, F, sigma, virial_atom, E, st);
 }

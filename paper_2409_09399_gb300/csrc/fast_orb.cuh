@@ -1,0 +1,131 @@
+// fast_orb.cuh -- FP32 orbital values (and gradients) for the tensor-core
+// producers: no per-orbital local arrays, species data in shared memory, one
+// 16-byte table load per radial function, each orbital handed to a callback
+// as soon as it is formed.
+//
+// phi_{l m}(d) = u(r) S_lm(d), u = R(r) / r^l, with R the cubic on the knot
+// interval (R = c0 + t (c1 + t (c2 + t c3)), t = r/dr - k) and S_lm the real
+// solid harmonics (normalised Y_lm, no Condon-Shortley phase).
+// grad phi = u'(r) (d / r) S_lm + u grad S_lm, u' = (R' - l R / r) / r^l.
+#pragma once
+
+#include "gint_impl.cuh"
+
+namespace gint {
+
+struct SpeciesFast {
+    int n_radial;
+    int n_int;
+    int lmax;
+    int nw;
+    float rc2;
+    float inv_dr;
+    int coef4;            // offset of the species' table in float4 units
+    int rad_l[kMaxRadial];
+    int orb_base[kMaxRadial];  // first orbital of each radial function
+};
+
+__device__ __forceinline__ void species_fast_from(const SpeciesDev& s, SpeciesFast& f) {
+    f.n_radial = s.n_radial;
+    f.n_int = s.n_int;
+    f.lmax = s.lmax;
+    f.nw = s.n_orb;
+    f.rc2 = s.rc_f * s.rc_f;
+    f.inv_dr = s.inv_dr_f;
+    f.coef4 = (int)(s.tab_off >> 2);
+    for (int j = 0; j < kMaxRadial; ++j) { f.rad_l[j] = j < s.n_radial ? s.rad_l[j] : 0; f.orb_base[j] = 0; }
+    // orbital order: l ascending, radial functions in input order, m = -l..l
+    int o = 0;
+    for (int l = 0; l <= kMaxL; ++l)
+        for (int j = 0; j < s.n_radial; ++j)
+            if (s.rad_l[j] == l) { f.orb_base[j] = o; o += 2 * l + 1; }
+}
+
+// Calls put(o, phi, gx, gy, gz) for every orbital o of the species at
+// displacement d (the gradient arguments are meaningful only with kGrad);
+// returns false (no calls) when |d| >= rc.
+template <bool kGrad, typename Put>
+__device__ __forceinline__ bool orbitals_fast(const SpeciesFast& s, const float4* __restrict__ coef, float dx,
+                                              float dy, float dz, Put&& put) {
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 >= s.rc2) return false;
+    const bool tiny = r2 < 1e-20f;
+    const float r = sqrtf(r2);
+    const float rinv = tiny ? 0.f : 1.f / r;
+    float x = r * s.inv_dr;
+    int k = (int)x;
+    k = min(k, s.n_int - 1);
+    const float t = x - (float)k;
+    // real solid harmonics up to l = 3 (normalisation as in the orbital definition)
+    const float xx = dx * dx, yy = dy * dy, zz = dz * dz;
+    const float k00 = 0.28209479177387814f, k1 = 0.48860251190291992f;
+    const float k2a = 1.0925484305920792f, k2b = 0.31539156525252005f, k2c = 0.54627421529603959f;
+    const float k3a = 0.59004358992664352f, k3b = 2.8906114426405538f, k3c = 0.45704579946446572f;
+    const float k3d = 0.37317633259011540f, k3e = 1.4453057213202769f;
+    const float4* cf = coef + s.coef4 + k * s.n_radial;
+    for (int j = 0; j < s.n_radial; ++j) {
+        const float4 c = __ldg(cf + j);
+        const int l = s.rad_l[j];
+        const int o = s.orb_base[j];
+        float R = c.x + t * (c.y + t * (c.z + t * c.w));
+        float dR = 0.f;
+        if (kGrad) dR = (c.y + t * (2.f * c.z + t * (3.f * c.w))) * s.inv_dr;
+        if (tiny) {
+            // limits at the atom centre: phi = R(0) Y00 for l = 0, zero for l >= 1;
+            // grad phi = R'(0) grad S_1m for l = 1, zero otherwise (c.y / dr = R'(0))
+            if (l == 0) {
+                put(o, R * k00, 0.f, 0.f, 0.f);
+            } else if (l == 1) {
+                const float g = c.y * s.inv_dr * k1;
+                put(o + 0, 0.f, 0.f, g, 0.f);
+                put(o + 1, 0.f, 0.f, 0.f, g);
+                put(o + 2, 0.f, g, 0.f, 0.f);
+            } else {
+                for (int m = 0; m < 2 * l + 1; ++m) put(o + m, 0.f, 0.f, 0.f, 0.f);
+            }
+            continue;
+        }
+        float rl = 1.f;
+        for (int q = 0; q < l; ++q) rl *= rinv;
+        const float u = R * rl;
+        const float a = kGrad ? (dR - (float)l * R * rinv) * rl * rinv : 0.f;  // u'/r
+        if (l == 0) {
+            put(o, u * k00, a * k00 * dx, a * k00 * dy, a * k00 * dz);
+        } else if (l == 1) {
+            const float sy = k1 * dy, sz = k1 * dz, sx = k1 * dx;
+            put(o + 0, u * sy, a * sy * dx, a * sy * dy + u * k1, a * sy * dz);
+            put(o + 1, u * sz, a * sz * dx, a * sz * dy, a * sz * dz + u * k1);
+            put(o + 2, u * sx, a * sx * dx + u * k1, a * sx * dy, a * sx * dz);
+        } else if (l == 2) {
+            const float s4 = k2a * dx * dy, s5 = k2a * dy * dz, s6 = k2b * (2.f * zz - xx - yy);
+            const float s7 = k2a * dx * dz, s8 = k2c * (xx - yy);
+            put(o + 0, u * s4, a * s4 * dx + u * k2a * dy, a * s4 * dy + u * k2a * dx, a * s4 * dz);
+            put(o + 1, u * s5, a * s5 * dx, a * s5 * dy + u * k2a * dz, a * s5 * dz + u * k2a * dy);
+            put(o + 2, u * s6, a * s6 * dx - u * 2.f * k2b * dx, a * s6 * dy - u * 2.f * k2b * dy,
+                a * s6 * dz + u * 4.f * k2b * dz);
+            put(o + 3, u * s7, a * s7 * dx + u * k2a * dz, a * s7 * dy, a * s7 * dz + u * k2a * dx);
+            put(o + 4, u * s8, a * s8 * dx + u * 2.f * k2c * dx, a * s8 * dy - u * 2.f * k2c * dy, a * s8 * dz);
+        } else {
+            const float q5 = 4.f * zz - xx - yy;
+            const float s9 = k3a * dy * (3.f * xx - yy), s10 = k3b * dx * dy * dz, s11 = k3c * dy * q5;
+            const float s12 = k3d * dz * (2.f * zz - 3.f * xx - 3.f * yy), s13 = k3c * dx * q5;
+            const float s14 = k3e * dz * (xx - yy), s15 = k3a * dx * (xx - 3.f * yy);
+            put(o + 0, u * s9, a * s9 * dx + u * k3a * 6.f * dx * dy, a * s9 * dy + u * k3a * 3.f * (xx - yy), a * s9 * dz);
+            put(o + 1, u * s10, a * s10 * dx + u * k3b * dy * dz, a * s10 * dy + u * k3b * dx * dz,
+                a * s10 * dz + u * k3b * dx * dy);
+            put(o + 2, u * s11, a * s11 * dx - u * k3c * 2.f * dx * dy, a * s11 * dy + u * k3c * (q5 - 2.f * yy),
+                a * s11 * dz + u * k3c * 8.f * dy * dz);
+            put(o + 3, u * s12, a * s12 * dx - u * k3d * 6.f * dx * dz, a * s12 * dy - u * k3d * 6.f * dy * dz,
+                a * s12 * dz + u * k3d * (6.f * zz - 3.f * xx - 3.f * yy));
+            put(o + 4, u * s13, a * s13 * dx + u * k3c * (q5 - 2.f * xx), a * s13 * dy - u * k3c * 2.f * dx * dy,
+                a * s13 * dz + u * k3c * 8.f * dx * dz);
+            put(o + 5, u * s14, a * s14 * dx + u * k3e * 2.f * dx * dz, a * s14 * dy - u * k3e * 2.f * dy * dz,
+                a * s14 * dz + u * k3e * (xx - yy));
+            put(o + 6, u * s15, a * s15 * dx + u * k3a * 3.f * (xx - yy), a * s15 * dy - u * k3a * 6.f * dx * dy,
+                a * s15 * dz);
+        }
+    }
+    return true;
+}
+
+}  // namespace gint

@@ -78,6 +78,7 @@ struct Problem {
     const int64_t* offsets;      // n_blocks + 1
     const int64_t* row_start;    // n_atoms + 1
     int n_atoms;
+    int n_species;
     int* err;                    // device error flags (bit set)
 };
 
@@ -127,6 +128,7 @@ struct gint_handle {
     int* d_nw_atom = nullptr;         // orbitals of every atom
     double* d_facc = nullptr;         // per-atom force and virial accumulators, n_atoms x 12
     double* d_red = nullptr;          // small FP64 reduction buffer ([0] energy)
+    void* d_dt = nullptr;             // per-call 16x16 tensor-core copy of D (1 KB per block)
     void* d_scratch = nullptr;
     size_t scratch_bytes = 0;
     int n_ctas = 0;                   // persistent CTAs of the SIMT kernels
@@ -147,6 +149,7 @@ struct gint_handle {
         p.offsets = d_offsets;
         p.row_start = d_row_start;
         p.n_atoms = n_atoms;
+        p.n_species = n_species;
         p.err = d_err;
         return p;
     }

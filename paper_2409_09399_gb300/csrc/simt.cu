@@ -563,3 +563,4 @@ gint_status launch_force_finalize(gint_handle* h, double* F, double* sigma, doub
 }
 
 }  // namespace gint
+

@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "fast_orb.cuh"
 #include "gint_impl.cuh"
 #include "tc_ptx.cuh"
 
@@ -32,6 +33,8 @@ constexpr int kTcChunk = 16;        // points per K chunk (one MMA K step)
 constexpr int kTcMaxRows = 640;     // padded brick orbitals (5 tiles of 128)
 constexpr int kTcMaxAtoms = 64;     // atom images per brick
 constexpr int kTcMaxPairsPerPass = 4;
+constexpr int kTcMaxPts = 1024;     // points per brick on this path
+constexpr int kTcMaxSpecies = 8;
 constexpr long kWaitLimit = 1L << 26;  // bounded mbarrier polls
 
 // bytes of one 16-bit operand piece for one chunk: rows x 16 points x 2 B
@@ -56,7 +59,8 @@ struct TcSmem {
     unsigned char buf[2][kBufBytes];
     TcAtom at[kTcMaxAtoms];
     int64_t pairoff[kTcMaxAtoms * kTcMaxAtoms];
-    float W[kMaxBrickPts];          // 2^s V dV
+    float4 pt[kTcMaxPts];           // in-brick offset of each point (x, y, z) and 2^s V dV
+    SpeciesFast spf[kTcMaxSpecies];
     unsigned char row_atom[kTcMaxRows];
     unsigned char row_mu[kTcMaxRows];
     uint64_t bar[2];
@@ -111,11 +115,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         S.abort = 0;
     }
+    if (tid < P.n_species) species_fast_from(P.sp[tid], S.spf[tid]);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = S.tmem;
     uint32_t commits[2] = {0, 0};  // completed-phase counters per buffer (same in every thread)
+    const float4* coef4 = reinterpret_cast<const float4*>(P.coef32);
 
     for (;;) {
         if (tid == 0) S.work = atomicAdd(A.counter, 1);
@@ -144,14 +150,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
             a.nw = P.sp[X.species].n_orb;
             a.t[0] = X.t[0]; a.t[1] = X.t[1]; a.t[2] = X.t[2];
         }
-        // weights and their power-of-two scale (max |2^s W| in [0.5, 1))
+        // in-brick point offsets, weights and their power-of-two scale (max |2^s W| in [0.5, 1))
         float wmax = 0.f;
         for (int p = tid; p < g.bpad; p += kTcThreads) {
             int g0, g1, g2;
             float wv = 0.f;
             if (brick_point(g, b0, b1, b2, p, g0, g1, g2))
                 wv = (float)(V[((int64_t)g0 * g.n[1] + g1) * g.n[2] + g2] * g.dV);
-            S.W[p] = wv;
+            const int l2 = p % g.B[2], l1 = (p / g.B[2]) % g.B[1], l0 = p / (g.B[2] * g.B[1]);
+            float4 q4;
+            q4.x = (float)l0 * (float)g.step[0][0] + (float)l1 * (float)g.step[1][0] + (float)l2 * (float)g.step[2][0];
+            q4.y = (float)l0 * (float)g.step[0][1] + (float)l1 * (float)g.step[1][1] + (float)l2 * (float)g.step[2][1];
+            q4.z = (float)l0 * (float)g.step[0][2] + (float)l1 * (float)g.step[1][2] + (float)l2 * (float)g.step[2][2];
+            q4.w = wv;
+            S.pt[p] = q4;
             wmax = fmaxf(wmax, fabsf(wv));
         }
         for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
@@ -173,7 +185,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
         }
         __syncthreads();
         const float wscale = 1.f / S.scale_inv;
-        for (int p = tid; p < g.bpad; p += kTcThreads) S.W[p] *= wscale;
+        for (int p = tid; p < g.bpad; p += kTcThreads) S.pt[p].w *= wscale;
         int nrow = 0;
         for (int i = 0; i < na; ++i) nrow += S.at[i].nw;
         const int nt = (nrow + 127) >> 7;
@@ -183,15 +195,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
             if (a1 > a2) continue;
             int64_t off = -1;
             const TcAtom &X = S.at[a1], &Y = S.at[a2];
-            const double dx = (double)Y.c_hi[0] - X.c_hi[0] + ((double)Y.c_lo[0] - X.c_lo[0]);
-            const double dy = (double)Y.c_hi[1] - X.c_hi[1] + ((double)Y.c_lo[1] - X.c_lo[1]);
-            const double dz = (double)Y.c_hi[2] - X.c_hi[2] + ((double)Y.c_lo[2] - X.c_lo[2]);
-            const double dist = sqrt(dx * dx + dy * dy + dz * dz);
-            const double cut = P.sp[X.sp].rc + P.sp[Y.sp].rc;
-            if (dist < cut + 1e-6) {
+            // FP32 distance with a margin: only pairs within rc1 + rc2 are looked up
+            const float dx = (Y.c_hi[0] - X.c_hi[0]) + (Y.c_lo[0] - X.c_lo[0]);
+            const float dy = (Y.c_hi[1] - X.c_hi[1]) + (Y.c_lo[1] - X.c_lo[1]);
+            const float dz = (Y.c_hi[2] - X.c_hi[2]) + (Y.c_lo[2] - X.c_lo[2]);
+            const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+            const float cut = P.sp[X.sp].rc_f + P.sp[Y.sp].rc_f;
+            if (dist < cut + 1e-3f) {
                 const int64_t blk = find_block(P, X.I, Y.I, Y.t[0] - X.t[0], Y.t[1] - X.t[1], Y.t[2] - X.t[2]);
                 if (blk >= 0) off = P.offsets[blk];
-                else if (dist < cut - 1e-6) atomicOr(P.err, kErrPatternMissing);
+                else if (dist < cut - 1e-3f) atomicOr(P.err, kErrPatternMissing);
             }
             S.pairoff[a1 * na + a2] = off;
         }
@@ -210,6 +223,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
         const int nchunks = g.bpad / kTcChunk;
         for (int pass0 = 0; pass0 < npairs && !S.abort; pass0 += kTcMaxPairsPerPass) {
             const int pass_n = min(kTcMaxPairsPerPass, npairs - pass0);
+            // tiles whose rows this pass reads; only atom images with rows in them are produced
+            unsigned need = 0;
+            {
+                int pi = 0, pj = 0;
+                for (int t = 0; t < pass0 + pass_n; ++t) {
+                    if (t >= pass0) need |= (1u << pi) | (1u << pj);
+                    if (++pj >= nt) { ++pi; pj = pi; }
+                }
+            }
             for (int c = 0; c < nchunks; ++c) {
                 const int b = c & 1;
                 // the MMAs of the chunk that last used this buffer must be done
@@ -218,36 +240,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
                         if (lane == 0) atomicOr(&S.abort, 1);
                     }
                 }
-                // orbital values of every atom image at the chunk's 16 points
+                // orbital values of the needed atom images at the chunk's 16 points
                 unsigned char* buf = S.buf[b];
                 for (int item = tid; item < na * kTcChunk; item += kTcThreads) {
                     const int a = item / kTcChunk, q = item - a * kTcChunk;
-                    const int p = c * kTcChunk + q;
                     const TcAtom& X = S.at[a];
-                    const int l2 = p % g.B[2], l1 = (p / g.B[2]) % g.B[1], l0 = p / (g.B[2] * g.B[1]);
-                    float phi[kMaxNw];
-                    bool inside = false;
-                    if (p < g.bpts) {
-                        const float fx = (float)l0 * (float)g.step[0][0] + (float)l1 * (float)g.step[1][0] + (float)l2 * (float)g.step[2][0];
-                        const float fy = (float)l0 * (float)g.step[0][1] + (float)l1 * (float)g.step[1][1] + (float)l2 * (float)g.step[2][1];
-                        const float fz = (float)l0 * (float)g.step[0][2] + (float)l1 * (float)g.step[1][2] + (float)l2 * (float)g.step[2][2];
-                        const float dx = (X.c_hi[0] + fx) + X.c_lo[0];
-                        const float dy = (X.c_hi[1] + fy) + X.c_lo[1];
-                        const float dz = (X.c_hi[2] + fz) + X.c_lo[2];
-                        inside = eval_atom<float, false>(P, P.sp[X.sp], dx, dy, dz, phi, nullptr);
-                    }
-                    const float wv = S.W[p];
-                    for (int o = 0; o < X.nw; ++o) {
-                        const float v = inside ? phi[o] : 0.f;
+                    const int t0 = X.off >> 7, t1 = (X.off + X.nw - 1) >> 7;
+                    if (!((need >> t0) & 1u) && !((need >> t1) & 1u)) continue;
+                    const int p = c * kTcChunk + q;
+                    const float4 q4 = S.pt[p];
+                    const float dx = (X.c_hi[0] + q4.x) + X.c_lo[0];
+                    const float dy = (X.c_hi[1] + q4.y) + X.c_lo[1];
+                    const float dz = (X.c_hi[2] + q4.z) + X.c_lo[2];
+                    const float wv = q4.w;
+                    const int rbase = X.off;
+                    auto put = [&](int o, float v, float, float, float) {
                         unsigned short ah, al, bh, bl;
                         Conv<H16>::split(v * wv, ah, al);
                         Conv<H16>::split(v, bh, bl);
-                        const int off = piece_off(X.off + o, q);
+                        const int off = piece_off(rbase + o, q);
                         *reinterpret_cast<unsigned short*>(&buf[0 * kPieceBytes + off]) = ah;
                         *reinterpret_cast<unsigned short*>(&buf[1 * kPieceBytes + off]) = al;
                         *reinterpret_cast<unsigned short*>(&buf[2 * kPieceBytes + off]) = bh;
                         *reinterpret_cast<unsigned short*>(&buf[3 * kPieceBytes + off]) = bl;
-                    }
+                    };
+                    const bool inside = p < g.bpts && orbitals_fast<false>(S.spf[X.sp], coef4, dx, dy, dz, put);
+                    if (!inside)
+                        for (int o = 0; o < X.nw; ++o) {
+                            const int off = piece_off(rbase + o, q);
+                            for (int pc = 0; pc < 4; ++pc) *reinterpret_cast<unsigned short*>(&buf[pc * kPieceBytes + off]) = 0;
+                        }
                 }
                 tc::fence_async_smem();
                 __syncthreads();
@@ -319,7 +341,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
                                 const int64_t off = S.pairoff[a1 * na + a2];
                                 if (off < 0) continue;
                                 const int nu = S.row_mu[col];
-                                const double val = (double)v[jj] * (double)sinv;
+                                const double val = (double)(v[jj] * sinv);  // sinv is a power of two: exact
                                 const int nw2 = S.at[a2].nw;
                                 if (a1 == a2) {
                                     // same atom image: the block is symmetric; the tile grid only holds
@@ -355,10 +377,11 @@ size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
 
 gint_status tc_vlocal(gint_handle* h, int bf16, const double* V, double* H, cudaStream_t st) {
     if (h->n_work == 0) return GINT_OK;
-    if (h->max_brick_orb > kTcMaxRows || h->max_brick_atoms > kTcMaxAtoms || h->grid.bpad > kMaxBrickPts ||
-        h->grid.bpad % kTcChunk != 0) {
-        set_error("tensor-core form needs <= %d orbitals and <= %d atom images per brick (have %d, %d); "
-                  "use smaller bricks", kTcMaxRows, kTcMaxAtoms, h->max_brick_orb, h->max_brick_atoms);
+    if (h->max_brick_orb > kTcMaxRows || h->max_brick_atoms > kTcMaxAtoms || h->grid.bpad > kTcMaxPts ||
+        h->grid.bpad % kTcChunk != 0 || h->n_species > kTcMaxSpecies) {
+        set_error("tensor-core form needs <= %d orbitals, <= %d atom images and <= %d points per brick and "
+                  "<= %d species (have %d, %d, %d, %d); use smaller bricks", kTcMaxRows, kTcMaxAtoms, kTcMaxPts,
+                  kTcMaxSpecies, h->max_brick_orb, h->max_brick_atoms, h->grid.bpad, h->n_species);
         return GINT_ERR_UNSUPPORTED;
     }
     TcArgs A;

@@ -1,0 +1,476 @@
+// tc_rho.cu -- tensor-core (tcgen05) form of rho (Eq. 3) and of the Pulay
+// force and stress (Eq. 4, 5).
+//
+// Both need, at every point p of a brick, G_p = Psi_p D_b (Psi_p: orbital
+// values at p over the brick's atom images, D_b the density-matrix blocks of
+// those images).  Per 128-point M-tile of a brick:
+//   * the tile's active atom images (non-zero somewhere in the tile) are
+//     listed; their orbitals are packed densely as the N dimension
+//     (<= 512 TMEM columns);
+//   * the K dimension runs over active atom images, one MMA K-step (16) per
+//     image (nw <= 16 orbitals, zero padded): A = Psi restricted to that
+//     image (128 points x 16), B = the image's D blocks against every active
+//     image, copied row by row from a per-call pre-formatted copy of D
+//     (every pattern block as a 16 x 16 tile of hi/lo 16-bit pieces in
+//     K-major core-matrix order), so a B row is two 16-byte copies per piece;
+//   * G accumulates in TMEM (lane = point), three products per step
+//     (hi*hi + hi*lo + lo*hi);
+//   * the epilogue thread of point p reads G_p, re-evaluates the orbital
+//     values (and gradients for the force) of every active image at p and
+//     forms rho_p = sum phi G, or F_I += 2 W_p grad phi . G with the virial
+//     and the energy, reduced per image in shared memory before FP64 atomics.
+#include <algorithm>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "fast_orb.cuh"
+#include "gint_impl.cuh"
+#include "tc_ptx.cuh"
+
+namespace gint {
+
+namespace {
+constexpr int kThreads = 256;
+constexpr int kMaxAtoms = 64;
+constexpr int kMaxCols = 512;            // TMEM columns (packed orbitals of one M-tile)
+constexpr int kBRowsMax = 512;
+constexpr int kAPiece = 128 * 16 * 2;    // 128 points x 16 orbitals x 2 B
+constexpr int kBPiece = kBRowsMax * 16 * 2;
+constexpr long kWait = 1L << 26;
+constexpr int kMaxSpecies = 8;
+
+struct Atom {
+    float c_hi[3], c_lo[3];  // brick origin - image position (FP64 split into two FP32 words)
+    int I, sp, nw;
+    int t[3];
+};
+
+struct Smem {
+    unsigned char A[2][2 * kAPiece];   // [buffer][hi | lo]
+    unsigned char B[2][2 * kBPiece];
+    Atom at[kMaxAtoms];
+    int pairblk[kMaxAtoms * kMaxAtoms];  // block (I_a2, I_a1, T_a1 - T_a2) for K image a1, N image a2; -1 if none
+    float W2[kMaxBrickPts];              // 2 V dV (force)
+    double red[kMaxAtoms][13];           // per-image F(3), virial(9), energy
+    float Gst[4][32][17];                // epilogue: G values of one image per lane (padded row)
+    float rho_part[128];                 // rho of the tile's points over earlier column groups
+    SpeciesFast spf[kMaxSpecies];
+    unsigned char act[kMaxAtoms];
+    int rowoff[kMaxAtoms + 1];
+    unsigned long long active_mask;
+    uint64_t bar[2];
+    uint32_t tmem;
+    int work, abort, nact, ncols;
+};
+
+template <typename H16> struct Split;
+template <> struct Split<__half> {
+    static __device__ __forceinline__ void run(float x, unsigned short& hi, unsigned short& lo) {
+        __half h = __float2half_rn(x);
+        hi = __half_as_ushort(h);
+        lo = __half_as_ushort(__float2half_rn(x - __half2float(h)));
+    }
+    static constexpr int bf16 = 0;
+};
+template <> struct Split<__nv_bfloat16> {
+    static __device__ __forceinline__ void run(float x, unsigned short& hi, unsigned short& lo) {
+        __nv_bfloat16 h = __float2bfloat16_rn(x);
+        hi = __bfloat16_as_ushort(h);
+        lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+    }
+    static constexpr int bf16 = 1;
+};
+
+// byte offset of element (row r, k) in a K-major piece with 16 K-columns:
+// core (r/8, k/8) at ((r/8)*2 + k/8)*128, row r%8 at *16, column k%8 at *2
+__device__ __forceinline__ int kmaj16(int r, int k) { return ((((r >> 3) << 1) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1); }
+
+__device__ __forceinline__ void point_offset(const GridDev& g, int p, float& fx, float& fy, float& fz) {
+    const int l2 = p % g.B[2], l1 = (p / g.B[2]) % g.B[1], l0 = p / (g.B[2] * g.B[1]);
+    fx = (float)l0 * (float)g.step[0][0] + (float)l1 * (float)g.step[1][0] + (float)l2 * (float)g.step[2][0];
+    fy = (float)l0 * (float)g.step[0][1] + (float)l1 * (float)g.step[1][1] + (float)l2 * (float)g.step[2][1];
+    fz = (float)l0 * (float)g.step[0][2] + (float)l1 * (float)g.step[1][2] + (float)l2 * (float)g.step[2][2];
+}
+}  // namespace
+
+// Pre-format D: every block b as a 16 x 16 tile (zero padded) of hi and lo
+// 16-bit pieces in K-major core-matrix order, values of block b taken from its
+// canonical block (transposed when b is not canonical).  One warp per block.
+template <typename H16>
+__global__ void k_format_d(Problem P, const int32_t* mirror, const int* nw_atom, int64_t n_blocks, const double* D,
+                           unsigned char* Dt) {
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= n_blocks) return;
+    const int32_t* k = P.blocks + 5 * b;
+    const int I = k[0], J = k[1];
+    const bool canon = (I < J) || (I == J && (k[2] > 0 || (k[2] == 0 && (k[3] > 0 || (k[3] == 0 && k[4] >= 0)))));
+    const int64_t src = canon ? b : (int64_t)mirror[b];
+    const int nI = nw_atom[I], nJ = nw_atom[J];
+    const double* Ds = D + P.offsets[src < 0 ? b : src];
+    unsigned char* out = Dt + b * 1024;
+    for (int e = lane; e < 256; e += 32) {
+        const int i = e >> 4, j = e & 15;
+        float v = 0.f;
+        if (i < nI && j < nJ && src >= 0) v = (float)(canon ? Ds[i * nJ + j] : Ds[j * nI + i]);
+        unsigned short hi, lo;
+        Split<H16>::run(v, hi, lo);
+        const int o = kmaj16(i, j);
+        *reinterpret_cast<unsigned short*>(out + o) = hi;
+        *reinterpret_cast<unsigned short*>(out + 512 + o) = lo;
+    }
+}
+
+template <typename H16, bool kForce>
+__global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* counter, const double* V,
+                                                            const unsigned char* Dt, double* rho, double* facc,
+                                                            double* acc_e) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    const GridDev& g = P.g;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == 0) {
+        tc::tmem_alloc(&S.tmem, kMaxCols);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(&S.bar[0], 1);
+        tc::mbar_init(&S.bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        S.abort = 0;
+    }
+    if (tid < P.n_species) species_fast_from(P.sp[tid], S.spf[tid]);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = S.tmem;
+    uint32_t commits[2] = {0, 0};
+    uint32_t chunk = 0;  // global chunk counter (buffer parity)
+    const float4* coef4 = reinterpret_cast<const float4*>(P.coef32);
+
+    for (;;) {
+        if (tid == 0) S.work = atomicAdd(counter, 1);
+        __syncthreads();
+        const int w = S.work;
+        if (w >= P.n_work || S.abort) break;
+        const int brick = P.work[w];
+        int b0, b1, b2;
+        brick_coords(g, brick, b0, b1, b2);
+        const int64_t s0 = P.brick_start[brick];
+        const int na = (int)(P.brick_start[brick + 1] - s0);
+        const double ox = b0 * g.B[0] * g.step[0][0] + b1 * g.B[1] * g.step[1][0] + b2 * g.B[2] * g.step[2][0];
+        const double oy = b0 * g.B[0] * g.step[0][1] + b1 * g.B[1] * g.step[1][1] + b2 * g.B[2] * g.step[2][1];
+        const double oz = b0 * g.B[0] * g.step[0][2] + b1 * g.B[1] * g.step[1][2] + b2 * g.B[2] * g.step[2][2];
+        for (int i = tid; i < na; i += kThreads) {
+            const ExtAtom X = P.ext[P.brick_atoms[s0 + i]];
+            Atom& a = S.at[i];
+            const double c[3] = {ox - X.p[0], oy - X.p[1], oz - X.p[2]};
+            for (int q = 0; q < 3; ++q) {
+                a.c_hi[q] = (float)c[q];
+                a.c_lo[q] = (float)(c[q] - (double)a.c_hi[q]);
+            }
+            a.I = X.atom;
+            a.sp = X.species;
+            a.nw = P.sp[X.species].n_orb;
+            a.t[0] = X.t[0]; a.t[1] = X.t[1]; a.t[2] = X.t[2];
+        }
+        if (kForce) {
+            for (int p = tid; p < g.bpad; p += kThreads) {
+                int g0, g1, g2;
+                float wv = 0.f;
+                if (brick_point(g, b0, b1, b2, p, g0, g1, g2))
+                    wv = (float)(2.0 * V[((int64_t)g0 * g.n[1] + g1) * g.n[2] + g2] * g.dV);
+                S.W2[p] = wv;
+            }
+        }
+        __syncthreads();
+        // ordered pair table: B rows of N image a2 for K image a1 come from block (I_a2, I_a1, T_a1 - T_a2)
+        for (int q = tid; q < na * na; q += kThreads) {
+            const int a1 = q / na, a2 = q - a1 * na;
+            const Atom &X = S.at[a1], &Y = S.at[a2];
+            // FP32 distance with a margin: only pairs within rc1 + rc2 are looked up
+            const float dx = (Y.c_hi[0] - X.c_hi[0]) + (Y.c_lo[0] - X.c_lo[0]);
+            const float dy = (Y.c_hi[1] - X.c_hi[1]) + (Y.c_lo[1] - X.c_lo[1]);
+            const float dz = (Y.c_hi[2] - X.c_hi[2]) + (Y.c_lo[2] - X.c_lo[2]);
+            const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+            const float cut = P.sp[X.sp].rc_f + P.sp[Y.sp].rc_f;
+            int blk = -1;
+            if (dist < cut + 1e-3f) {
+                const int64_t f = find_block(P, Y.I, X.I, X.t[0] - Y.t[0], X.t[1] - Y.t[1], X.t[2] - Y.t[2]);
+                if (f >= 0) blk = (int)f;
+                else if (dist < cut - 1e-3f) atomicOr(P.err, kErrPatternMissing);
+            }
+            S.pairblk[q] = blk;
+        }
+        __syncthreads();
+
+        const int n_mtiles = (g.bpad + 127) / 128;
+        for (int mt = 0; mt < n_mtiles && !S.abort; ++mt) {
+            // ---- active atom images of this M-tile
+            if (tid == 0) S.active_mask = 0ull;
+            __syncthreads();
+            if (tid < 128) {
+                const int p = mt * 128 + tid;
+                float fx = 0.f, fy = 0.f, fz = 0.f;
+                const bool pv = p < g.bpts;
+                if (pv) point_offset(g, p, fx, fy, fz);
+                for (int a = 0; a < na; ++a) {
+                    const Atom& X = S.at[a];
+                    const float dx = (X.c_hi[0] + fx) + X.c_lo[0];
+                    const float dy = (X.c_hi[1] + fy) + X.c_lo[1];
+                    const float dz = (X.c_hi[2] + fz) + X.c_lo[2];
+                    const float rc = P.sp[X.sp].rc_f;
+                    const bool in = pv && (dx * dx + dy * dy + dz * dz < rc * rc);
+                    if (__ballot_sync(0xffffffffu, in) && lane == 0) atomicOr(&S.active_mask, 1ull << a);
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int n = 0, off = 0;
+                for (int a = 0; a < na; ++a)
+                    if (S.active_mask >> a & 1ull) {
+                        S.act[n] = (unsigned char)a;
+                        S.rowoff[n] = off;
+                        off += S.at[a].nw;
+                        ++n;
+                    }
+                S.rowoff[n] = off;
+                S.nact = n;
+            }
+            __syncthreads();
+            const int nact = S.nact;
+            if (nact == 0) {
+                if (!kForce && tid < 128) {
+                    const int p = mt * 128 + tid;
+                    int g0, g1, g2;
+                    if (brick_point(g, b0, b1, b2, p, g0, g1, g2)) rho[((int64_t)g0 * g.n[1] + g1) * g.n[2] + g2] = 0.0;
+                }
+                continue;
+            }
+            if (S.abort) break;
+            // column groups: consecutive active images whose orbitals fit the 512 TMEM columns
+            for (int cg0 = 0; cg0 < nact && !S.abort;) {
+            int cg1 = cg0;
+            while (cg1 < nact && S.rowoff[cg1 + 1] - S.rowoff[cg0] <= kMaxCols) ++cg1;
+            if (cg1 == cg0) cg1 = cg0 + 1;  // never taken (an image has <= 16 orbitals); keeps the loop finite
+            const int rbase = S.rowoff[cg0];
+            const int nrows = S.rowoff[cg1] - rbase;
+            const int ncols = (nrows + 15) & ~15;
+            // zero B padding rows [nrows, ncols) of both buffers (MMAs of earlier tiles are complete)
+            for (int e = tid; e < (ncols - nrows) * 2; e += kThreads) {
+                const int r = nrows + (e >> 1), half = e & 1;
+                for (int b = 0; b < 2; ++b)
+                    for (int pc = 0; pc < 2; ++pc)
+                        *reinterpret_cast<uint4*>(&S.B[b][pc * kBPiece + kmaj16(r, half * 8)]) = make_uint4(0, 0, 0, 0);
+            }
+            // ---- K loop over active images
+            for (int k = 0; k < nact; ++k, ++chunk) {
+                const int b = chunk & 1;
+                if (commits[b] > 0 && !tc::mbar_wait(&S.bar[b], (commits[b] - 1) & 1, kWait))
+                    if (lane == 0) atomicOr(&S.abort, 1);
+                const int a1 = S.act[k];
+                const Atom& X = S.at[a1];
+                if (tid < 128) {
+                    // A row p: orbital values of image a1 at point p (16 slots, zero padded)
+                    const int p = mt * 128 + tid;
+                    unsigned char* A0 = S.A[b];
+                    for (int o = X.nw; o < 16; ++o) {
+                        *reinterpret_cast<unsigned short*>(A0 + kmaj16(tid, o)) = 0;
+                        *reinterpret_cast<unsigned short*>(A0 + kAPiece + kmaj16(tid, o)) = 0;
+                    }
+                    bool inside = false;
+                    if (p < g.bpts) {
+                        float fx, fy, fz;
+                        point_offset(g, p, fx, fy, fz);
+                        const float dx = (X.c_hi[0] + fx) + X.c_lo[0];
+                        const float dy = (X.c_hi[1] + fy) + X.c_lo[1];
+                        const float dz = (X.c_hi[2] + fz) + X.c_lo[2];
+                        auto put = [&](int o, float v, float, float, float) {
+                            unsigned short hi, lo;
+                            Split<H16>::run(v, hi, lo);
+                            *reinterpret_cast<unsigned short*>(A0 + kmaj16(tid, o)) = hi;
+                            *reinterpret_cast<unsigned short*>(A0 + kAPiece + kmaj16(tid, o)) = lo;
+                        };
+                        inside = orbitals_fast<false>(S.spf[X.sp], coef4, dx, dy, dz, put);
+                    }
+                    if (!inside)
+                        for (int o = 0; o < X.nw; ++o) {
+                            *reinterpret_cast<unsigned short*>(A0 + kmaj16(tid, o)) = 0;
+                            *reinterpret_cast<unsigned short*>(A0 + kAPiece + kmaj16(tid, o)) = 0;
+                        }
+                } else {
+                    // B rows: for every active image a2, rows nu of block (I_a2, I_a1, T_a1 - T_a2)
+                    const int t2 = tid - 128;
+                    for (int e = t2; e < nrows * 4; e += 128) {
+                        const int r = e >> 2, part = e & 3;  // part: (piece, half)
+                        // image of row r: largest j in the group with rowoff[j] <= rbase + r
+                        int lo_j = cg0, hi_j = cg1 - 1;
+                        while (lo_j < hi_j) {
+                            const int mid = (lo_j + hi_j + 1) >> 1;
+                            if (S.rowoff[mid] <= rbase + r) lo_j = mid; else hi_j = mid - 1;
+                        }
+                        const int a2 = S.act[lo_j];
+                        const int nu = rbase + r - S.rowoff[lo_j];
+                        const int blk = S.pairblk[a1 * na + a2];
+                        const int pc = part >> 1, half = part & 1;
+                        uint4 v = make_uint4(0, 0, 0, 0);
+                        if (blk >= 0) v = __ldg(reinterpret_cast<const uint4*>(Dt + (int64_t)blk * 1024 + pc * 512 + kmaj16(nu, half * 8)));
+                        *reinterpret_cast<uint4*>(&S.B[b][pc * kBPiece + kmaj16(r, half * 8)]) = v;
+                    }
+                }
+                tc::fence_async_smem();
+                __syncthreads();
+                if (S.abort) break;
+                if (tid == 0) {
+                    tc::fence_after_sync();
+                    const uint32_t a_hi = tc::smem_u32(S.A[b]), a_lo = a_hi + kAPiece;
+                    const uint32_t bb = tc::smem_u32(S.B[b]);
+                    for (int n0 = 0; n0 < ncols; n0 += 256) {
+                        const int nn = min(256, ncols - n0);
+                        const uint32_t idesc = tc::idesc_f16(128, nn, Split<H16>::bf16, 0, 0);
+                        const uint32_t b_hi = bb + (n0 >> 3) * 256, b_lo = b_hi + kBPiece;
+                        const uint32_t d = tmem + (uint32_t)n0;
+                        // K-major, 16 K-columns: LBO (K-adjacent cores) 128 B, SBO (row groups) 256 B
+                        tc::mma_f16(d, tc::smem_desc(a_hi, 128, 256), tc::smem_desc(b_hi, 128, 256), idesc, k > 0 ? 1u : 0u);
+                        tc::mma_f16(d, tc::smem_desc(a_hi, 128, 256), tc::smem_desc(b_lo, 128, 256), idesc, 1u);
+                        tc::mma_f16(d, tc::smem_desc(a_lo, 128, 256), tc::smem_desc(b_hi, 128, 256), idesc, 1u);
+                    }
+                    tc::mma_commit(&S.bar[b]);
+                }
+                commits[b] += 1;
+            }
+            // ---- all MMAs of this tile complete
+            for (int b = 0; b < 2; ++b)
+                if (commits[b] > 0 && !tc::mbar_wait(&S.bar[b], (commits[b] - 1) & 1, kWait))
+                    if (lane == 0) atomicOr(&S.abort, 1);
+            tc::fence_after_sync();
+            if (kForce) {
+                for (int e = tid; e < kMaxAtoms * 13; e += kThreads) (&S.red[0][0])[e] = 0.0;
+            }
+            __syncthreads();
+            if (S.abort) break;
+            // ---- epilogue: warps 0-3, lane = point
+            if (warp < 4) {
+                const int p = mt * 128 + tid;
+                int g0 = 0, g1 = 0, g2 = 0;
+                const bool pv = brick_point(g, b0, b1, b2, p, g0, g1, g2);
+                float fx = 0.f, fy = 0.f, fz = 0.f;
+                if (p < g.bpts) point_offset(g, p, fx, fy, fz);
+                float rho_p = cg0 == 0 ? 0.f : S.rho_part[tid];
+                for (int j = cg0; j < cg1; ++j) {
+                    const int a2 = S.act[j];
+                    const Atom& Y = S.at[a2];
+                    int c0 = S.rowoff[j] - rbase;
+                    int sh = 0;
+                    if (c0 + 16 > kMaxCols) { sh = c0 + 16 - kMaxCols; c0 -= sh; }
+                    float Gv[16];
+                    tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, Gv);
+                    float* gs = S.Gst[warp][lane];
+#pragma unroll
+                    for (int o = 0; o < 16; ++o) gs[o] = Gv[o];
+                    const float dx = (Y.c_hi[0] + fx) + Y.c_lo[0];
+                    const float dy = (Y.c_hi[1] + fy) + Y.c_lo[1];
+                    const float dz = (Y.c_hi[2] + fz) + Y.c_lo[2];
+                    float e_j = 0.f, f0 = 0.f, f1 = 0.f, f2 = 0.f;
+                    if (pv) {
+                        auto put = [&](int o, float v, float gx, float gy, float gz) {
+                            const float gv = gs[o + sh];
+                            e_j += v * gv;
+                            if (kForce) { f0 += gx * gv; f1 += gy * gv; f2 += gz * gv; }
+                        };
+                        (void)orbitals_fast<kForce>(S.spf[Y.sp], coef4, dx, dy, dz, put);
+                    }
+                    rho_p += e_j;
+                    if (kForce) {
+                        // per point in FP32, summed over the warp's 32 points in FP32,
+                        // then accumulated per image in FP64
+                        const float w2 = pv ? S.W2[p] : 0.f;
+                        float v[13];
+                        v[0] = w2 * f0; v[1] = w2 * f1; v[2] = w2 * f2;
+                        const float d3[3] = {dx, dy, dz};
+                        for (int a = 0; a < 3; ++a)
+                            for (int c = 0; c < 3; ++c) v[3 + 3 * a + c] = v[a] * d3[c];
+                        v[12] = 0.5f * w2 * e_j;
+                        for (int o = 16; o > 0; o >>= 1)
+                            for (int q = 0; q < 13; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+                        if (lane == 0)
+                            for (int q = 0; q < 13; ++q) atomicAdd(&S.red[j][q], (double)v[q]);
+                    }
+                }
+                S.rho_part[tid] = rho_p;
+                if (!kForce && pv && cg1 == nact) rho[((int64_t)g0 * g.n[1] + g1) * g.n[2] + g2] = (double)rho_p;
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+            if (kForce) {
+                for (int e = tid; e < nact * 13; e += kThreads) {
+                    const int j = e / 13, q = e - j * 13;
+                    const double v = S.red[j][q];
+                    if (v == 0.0) continue;
+                    if (q < 12) atomicAdd(facc + 12 * (size_t)S.at[S.act[j]].I + q, v);
+                    else atomicAdd(acc_e, v);
+                }
+                __syncthreads();
+            }
+            cg0 = cg1;
+            }  // column groups
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int b = 0; b < 2; ++b)
+        if (commits[b] > 0) (void)tc::mbar_wait(&S.bar[b], (commits[b] - 1) & 1, kWait);
+    if (S.abort && tid == 0) atomicOr(P.err, kErrTimeout);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kMaxCols);
+}
+
+// ------------------------------------------------------------------ host
+static gint_status ensure_dt(gint_handle* h) {
+    if (h->d_dt) return GINT_OK;
+    const size_t bytes = (size_t)std::max<int64_t>(1, h->n_blocks) * 1024;
+    GINT_CUDA_TRY(cudaMalloc(&h->d_dt, bytes));
+    return GINT_OK;
+}
+
+gint_status tc_rhoforce(gint_handle* h, int bf16, bool force, const double* V, const double* D, double* rho,
+                        double* facc, double* acc_e, cudaStream_t st) {
+    if (h->max_brick_atoms > kMaxAtoms || h->max_nw > 16 || h->n_species > kMaxSpecies) {
+        set_error("tensor-core rho/force needs <= %d atom images per brick, <= 16 orbitals per atom and <= %d "
+                  "species (have %d, %d, %d); use smaller bricks", kMaxAtoms, kMaxSpecies, h->max_brick_atoms,
+                  h->max_nw, h->n_species);
+        return GINT_ERR_UNSUPPORTED;
+    }
+    gint_status s = ensure_dt(h);
+    if (s != GINT_OK) return s;
+    Problem P = h->problem();
+    if (h->n_blocks > 0) {
+        const int64_t threads = h->n_blocks * 32;
+        if (bf16) k_format_d<__nv_bfloat16><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(P, h->d_mirror, h->d_nw_atom, h->n_blocks, D, (unsigned char*)h->d_dt);
+        else k_format_d<__half><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(P, h->d_mirror, h->d_nw_atom, h->n_blocks, D, (unsigned char*)h->d_dt);
+        GINT_CUDA_TRY(cudaGetLastError());
+    }
+    if (h->n_work == 0) return GINT_OK;
+    int* counter = h->d_err + 2;
+    GINT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
+    const size_t smem = sizeof(Smem) + 1024;
+    const unsigned char* Dt = (const unsigned char*)h->d_dt;
+#define GINT_LAUNCH_RF(H16, F)                                                                                  \
+    do {                                                                                                        \
+        GINT_CUDA_TRY(cudaFuncSetAttribute(k_rhoforce_tc<H16, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                           (int)smem));                                                         \
+        k_rhoforce_tc<H16, F><<<h->sm_count, kThreads, smem, st>>>(P, counter, V, Dt, rho, facc, acc_e);        \
+    } while (0)
+    if (bf16) {
+        if (force) GINT_LAUNCH_RF(__nv_bfloat16, true); else GINT_LAUNCH_RF(__nv_bfloat16, false);
+    } else {
+        if (force) GINT_LAUNCH_RF(__half, true); else GINT_LAUNCH_RF(__half, false);
+    }
+#undef GINT_LAUNCH_RF
+    GINT_CUDA_TRY(cudaGetLastError());
+    return GINT_OK;
+}
+
+}  // namespace gint

@@ -1,0 +1,75 @@
+"""Full-size parity on sampled outputs: TBG cells of the benchmark, in the launch
+configuration bench.py times (8x8x8 bricks), against the FP64 oracle evaluated
+one output at a time (random pattern blocks of H, random grid points of rho,
+random atoms of F).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+# stated accuracy of each form (max abs for H and F, normwise for rho over the sample)
+TOL = {
+    "fp64": {"H": 1e-11, "rho": 1e-11, "F": 1e-10},
+    "fp16x3": {"H": 5e-5, "rho": 5e-5, "F": 5e-5},
+}
+
+
+def run_case(m, precision, n_blocks=12, n_points=400, n_atoms=2, seed=0):
+    import torch
+    from paper_2409_09399_gb300 import gint
+    s = synth.tbg(m)
+    g = gint.from_system(s, precision=precision, brick=(8, 8, 8))
+    V = synth.v_grid(s.grid, synth.plane_wave_params(), device="cuda")
+    blocks, offsets = g.pattern()
+    D = synth.d_fill_torch(blocks, offsets[:-1], g.n_values, s.pos, s.cell, s.nw(), "cuda")
+    H = g.vlocal(V)
+    rho = g.rho(D)
+    F, sigma, vir, E = g.force_stress(V, D)
+    g.sync()
+    # identities that hold at any size
+    e_tr = float(torch.dot(D, H).item())
+    Hn = H.cpu().numpy()
+    o = oracle.Oracle(s)
+    assert np.array_equal(blocks, o.blocks) and np.array_equal(offsets, o.offsets)
+    rng = np.random.default_rng(seed)
+    sel = rng.choice(len(blocks), n_blocks, replace=False)
+    onsite = np.nonzero((blocks[:, 0] == blocks[:, 1]) & (blocks[:, 2:] == 0).all(1))[0]
+    sel = np.concatenate([sel, rng.choice(onsite, 4, replace=False)])
+    Vn = V.cpu().numpy()
+    ref = o.vlocal_blocks(Vn, blocks[sel])
+    eH = max(float(np.max(np.abs(Hn[offsets[b]:offsets[b + 1]].reshape(r.shape) - r))) for b, r in zip(sel, ref))
+    Dor = synth.d_fill(o.blocks, o.offsets[:-1], o.n_values, s.pos, s.cell, s.nw())
+    idx = np.stack([rng.integers(0, n, n_points) for n in s.grid], 1)
+    idx[: n_points // 2, 2] = rng.integers(int(0.35 * s.grid[2]), int(0.65 * s.grid[2]), n_points // 2)
+    r_ref = o.rho_points(Dor, idx)
+    r_got = rho[idx[:, 0], idx[:, 1], idx[:, 2]].cpu().numpy()
+    eR = float(np.max(np.abs(r_got - r_ref)) / np.max(np.abs(r_ref)))
+    atoms = rng.choice(s.n_atoms, n_atoms, replace=False)
+    F_ref, _ = o.force(Vn, Dor, atoms=atoms)
+    eF = float(np.max(np.abs(F.cpu().numpy()[atoms] - F_ref)))
+    # E from the force call equals sum D . H (both on the GPU) to the form's accuracy
+    eE = abs(E.item() - e_tr) / abs(e_tr)
+    print(f"TBG m={m} {precision}: H {eH:.2e} rho {eR:.2e} F {eF:.2e} E-vs-Tr(DH) {eE:.2e}")
+    return eH, eR, eF, eE
+
+
+@pytest.mark.parametrize("m,precision", [(29, "fp16x3"), (5, "fp64"), (15, "fp16x3")])
+def test_fullsize_sampled(m, precision, cuda):
+    eH, eR, eF, eE = run_case(m, precision)
+    tol = TOL[precision]
+    assert eH < tol["H"]
+    assert eR < tol["rho"]
+    assert eF < tol["F"]
+    assert eE < (1e-10 if precision == "fp64" else 1e-4)
+
+
+@pytest.mark.slow
+def test_fullsize_fp64_m29(cuda):
+    """The plain FP64 form on the 10,444-atom cell (about 90 s on one GB300)."""
+    eH, eR, eF, eE = run_case(29, "fp64", n_blocks=8, n_points=300, n_atoms=1)
+    tol = TOL["fp64"]
+    assert eH < tol["H"] and eR < tol["rho"] and eF < tol["F"] and eE < 1e-10

@@ -57,3 +57,62 @@ def test_tc_vlocal_tbg_sampled(precision, cuda):
         err = max(err, np.max(np.abs(got - ref[k])))
     print(f"{precision} TBG m=2: max |H - H_ref| over {len(sel)} blocks = {err:.3e}")
     assert err < 5e-5
+
+
+@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3"])
+def test_tc_rho_force_diamond(precision, cuda):
+    """rho and force/stress on the tensor cores against the oracle (diamond, 3x3x4 bricks)."""
+    import torch
+    from paper_2409_09399_gb300 import gint
+    s, o, V, _ = diamond_case()
+    if "diamond_rf" not in _cache:
+        D = o.d_fill()
+        F, W = o.force(V, D)
+        _cache["diamond_rf"] = (D, o.rho(D), F, W)
+    D_or, rho_ref, F_ref, W_ref = _cache["diamond_rf"]
+    g = gint.from_system(s, precision=precision, brick=(3, 3, 4))
+    blocks, offsets = g.pattern()
+    assert np.array_equal(blocks, o.blocks)
+    D = torch.from_numpy(D_or).cuda()
+    Vt = torch.from_numpy(V).cuda()
+    rho = g.rho(D)
+    F, sigma, vir, E = g.force_stress(Vt, D)
+    g.sync()
+    e_rho = np.max(np.abs(rho.cpu().numpy() - rho_ref)) / np.max(np.abs(rho_ref))
+    e_F = np.max(np.abs(F.cpu().numpy() - F_ref))
+    sig_ref = -W_ref.sum(0) / o.omega
+    e_sig = np.max(np.abs(sigma.cpu().numpy() - sig_ref))
+    print(f"{precision}: rho normwise {e_rho:.3e}  F abs {e_F:.3e} (max {np.abs(F_ref).max():.3f})  sigma abs {e_sig:.3e}")
+    assert e_rho < 1e-4
+    assert e_F < 1e-4
+    assert e_sig < 1e-4
+
+
+@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3"])
+def test_tc_rho_force_tbg_sampled(precision, cuda):
+    import torch
+    from paper_2409_09399_gb300 import gint
+    s = synth.tbg(2)
+    o = oracle.Oracle(s)
+    V = synth.v_grid(s.grid, synth.plane_wave_params()).numpy()
+    g = gint.from_system(s, precision=precision, brick=(8, 8, 8))
+    blocks, offsets = g.pattern()
+    D = synth.d_fill_torch(blocks, offsets[:-1], g.n_values, s.pos, s.cell, s.nw(), "cuda")
+    Vt = torch.from_numpy(V).cuda()
+    rho = g.rho(D).cpu().numpy()
+    F, sigma, vir, E = g.force_stress(Vt, D)
+    g.sync()
+    rng = np.random.default_rng(3)
+    D_or = o.d_fill()
+    idx = np.stack([rng.integers(0, n, 2000) for n in s.grid], 1)
+    # points near the layers, where rho is not zero
+    idx[:, 2] = rng.integers(100, 180, 2000)
+    r_ref = o.rho_points(D_or, idx)
+    r_got = rho[idx[:, 0], idx[:, 1], idx[:, 2]]
+    e_rho = np.max(np.abs(r_got - r_ref)) / np.max(np.abs(r_ref))
+    atoms = np.array([0, 17, 40, 75])
+    F_ref, _ = o.force(V, D_or, atoms=atoms)
+    e_F = np.max(np.abs(F.cpu().numpy()[atoms] - F_ref))
+    print(f"{precision} TBG m=2: rho normwise {e_rho:.3e}  F abs {e_F:.3e} (max {np.abs(F_ref).max():.3f})")
+    assert e_rho < 1e-4
+    assert e_F < 1e-4
