@@ -147,6 +147,25 @@ gint_status gint_rho(gint_handle* h, const double* D, double* rho, gint_stream s
 gint_status gint_force_stress(gint_handle* h, const double* V, const double* D, double* F,
                               double* sigma, double* virial_atom, double* E, gint_stream stream);
 
+/* H^V in the FP64 form, like gint_vlocal(h, V, H, 0, stream), without any
+ * device allocation.  For callers that cannot let a library call cudaMalloc
+ * (it synchronises the device and fails once a framework's caching allocator
+ * has reserved the free memory): the kernel's orbital-value scratch is a fixed
+ * 64 MiB array inside libgint, present on every GPU that loads the library
+ * until the process exits.  The paper has no counterpart of this call.
+ *   - Always FP64, whatever gint_set_precision selected; H is overwritten.
+ *   - The first call on a device resolves the array's device address
+ *     (cudaGetSymbolAddress, with the handle's device current); make that first
+ *     call before any stream capture.
+ *   - A brick whose scratch slice exceeds 64 MiB is rejected with
+ *     GINT_ERR_UNSUPPORTED (use smaller bricks); with fewer slices than the
+ *     handle's CTA count the kernel runs on fewer CTAs.
+ *   - Every call, on every handle, shares the one array: calls whose kernels
+ *     overlap on the GPU race and give wrong results.  Nothing in the array
+ *     needs to start at zero (each brick's slice is written before it is read).
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine. */
+gint_status gint_vlocal_static(gint_handle* h, const double* V, double* H, gint_stream stream);
+
 /* Wait for the handle's work on `stream` and report (then clear) any flag a
  * device-side check raised since the last call. */
 gint_status gint_sync(gint_handle* h, gint_stream stream);

@@ -564,3 +564,23 @@ gint_status launch_force_finalize(gint_handle* h, double* F, double* sigma, doub
 
 }  // namespace gint
 
+namespace gint {
+// Launch the FP64 H^V SIMT kernel on caller-provided scratch (n_ctas slices of
+// `cta_stride` bytes).  Used by the entry point that allocates nothing.
+gint_status simt_vlocal_on_scratch(gint_handle* h, const double* V, double* H, char* scratch, size_t cta_stride,
+                                   int n_ctas, cudaStream_t st) {
+    if (h->n_work == 0) return GINT_OK;
+    SimtArgs A;
+    A.P = h->problem();
+    A.max_atoms = std::max(1, h->max_brick_atoms);
+    A.cta_stride = cta_stride;
+    A.scratch = scratch;
+    A.counter = h->d_err + 2;
+    GINT_CUDA_TRY(cudaMemsetAsync(A.counter, 0, sizeof(int), st));
+    const size_t smem = simt_smem_bytes(A.max_atoms, h->grid.bpad);
+    GINT_CUDA_TRY(cudaFuncSetAttribute(k_vlocal_simt<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_vlocal_simt<double><<<n_ctas, 256, smem, st>>>(A, V, H);
+    GINT_CUDA_TRY(cudaGetLastError());
+    return GINT_OK;
+}
+}  // namespace gint

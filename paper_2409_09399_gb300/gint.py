@@ -22,7 +22,8 @@ STATUS = {0: "GINT_OK", 1: "GINT_ERR_INVALID_ARG", 2: "GINT_ERR_CUDA", 3: "GINT_
 
 # exported symbols, in the order include/gint.h declares them
 SYMBOLS = ["gint_setup", "gint_destroy", "gint_pattern", "gint_set_precision", "gint_vlocal", "gint_rho",
-           "gint_force_stress", "gint_sync", "gint_get_info", "gint_work_stats", "gint_last_error"]
+           "gint_force_stress", "gint_vlocal_static", "gint_sync", "gint_get_info", "gint_work_stats",
+           "gint_last_error"]
 
 
 class GintError(RuntimeError):
@@ -81,6 +82,8 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.gint_rho.argtypes = [vp, vp, vp, vp]
     L.gint_force_stress.restype = i32
     L.gint_force_stress.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    L.gint_vlocal_static.restype = i32
+    L.gint_vlocal_static.argtypes = [vp, vp, vp, vp]
     L.gint_sync.restype = i32
     L.gint_sync.argtypes = [vp, vp]
     L.gint_get_info.restype = i32
