@@ -72,7 +72,11 @@ typedef enum {
     GINT_BF16X3 = 3,   /* H^V on the tensor cores: operands split x = hi + lo in bf16,
                           products hi*hi + hi*lo + lo*hi, FP32 accumulation per brick */
     GINT_BF16X6 = 4,   /* reserved */
-    GINT_FP16X3 = 5    /* as GINT_BF16X3 with fp16 pieces (22-bit products) */
+    GINT_FP16X3 = 5,   /* as GINT_BF16X3 with fp16 pieces (22-bit products) */
+    GINT_FP16X4 = 6    /* tensor cores, exact leading term: each operand value x of orbital o
+                          is x / 2^qe_o = n + l, n an integer of <= 8 bits (exact in fp16),
+                          l in fp16; the products n*n accumulate exactly in FP32, the cross
+                          terms n*l + l*n + l*l in a second FP32 accumulator */
 } gint_precision;
 
 /* One tabulated radial function R(r): y[k] = R(k*dr), dy[k] = R'(k*dr),
@@ -165,6 +169,24 @@ gint_status gint_force_stress(gint_handle* h, const double* V, const double* D, 
  *     needs to start at zero (each brick's slice is written before it is read).
  *   - Calls no cudaMalloc, cudaFree or other allocating routine. */
 gint_status gint_vlocal_static(gint_handle* h, const double* V, double* H, gint_stream stream);
+
+/* Many cells in one launch (the uneven multi-cell workload: many small
+ * periodic cells, each with its own handle).  gint_batch_create takes n
+ * handles of one device (the handles must outlive the batch).  gint_batch_run
+ * runs, for every cell i, gint_vlocal (if H[i]), gint_rho (if rho[i]) and
+ * gint_force_stress (if F[i], sigma[i] or E[i]); the pointer arrays are host
+ * arrays of n device pointers (H, rho, F, sigma, E may be NULL as a whole).
+ * The first call captures all these calls into one CUDA graph on an internal
+ * stream; later calls with the same buffers launch that graph as one unit,
+ * ordered after the work already queued on `stream` and before later work on
+ * it.  Changing a buffer re-captures.  Errors of the individual calls are
+ * reported as they would be by those calls. */
+typedef struct gint_batch gint_batch;
+gint_status gint_batch_create(int n, gint_handle* const* handles, gint_batch** out);
+gint_status gint_batch_run(gint_batch* b, const double* const* V, const double* const* D, double* const* H,
+                           double* const* rho, double* const* F, double* const* sigma, double* const* E,
+                           gint_stream stream);
+void gint_batch_destroy(gint_batch* b);
 
 /* Wait for the handle's work on `stream` and report (then clear) any flag a
  * device-side check raised since the last call. */

@@ -11,8 +11,8 @@ gint_status launch_mirror(gint_handle* h, double* H, cudaStream_t st);
 gint_status launch_rho_empty(gint_handle* h, double* rho, cudaStream_t st);
 gint_status launch_force_finalize(gint_handle* h, double* F, double* sigma, double* virial, double* E,
                                   cudaStream_t st);
-gint_status tc_vlocal(gint_handle* h, int bf16, const double* V, double* H, cudaStream_t st);
-gint_status tc_rhoforce(gint_handle* h, int bf16, bool force, const double* V, const double* D, double* rho,
+gint_status tc_vlocal(gint_handle* h, int form, const double* V, double* H, cudaStream_t st);
+gint_status tc_rhoforce(gint_handle* h, int form, bool force, const double* V, const double* D, double* rho,
                         double* facc, double* acc_e, cudaStream_t st);
 
 namespace {
@@ -30,10 +30,17 @@ struct DeviceGuard {
 };
 
 // FP64: SIMT FP64.  FP32: SIMT FP32.  BF16X3 / FP16X3: tensor cores (split
-// 16-bit operands, three products, FP32 accumulation per brick).
+// 16-bit operands, three products, FP32 accumulation per brick).  FP16X4:
+// tensor cores with an exactly accumulated 8-bit fixed-point leading product.
+bool is_tc(const gint_handle* h) {
+    return h->precision == GINT_BF16X3 || h->precision == GINT_FP16X3 || h->precision == GINT_FP16X4;
+}
+int tc_form(const gint_handle* h) { return h->precision == GINT_BF16X3 ? 1 : h->precision == GINT_FP16X4 ? 2 : 0; }
+
 gint_status check_precision(const gint_handle* h, bool* fp32) {
     if (h->precision == GINT_FP64) { *fp32 = false; return GINT_OK; }
-    if (h->precision == GINT_FP32 || h->precision == GINT_BF16X3 || h->precision == GINT_FP16X3) {
+    if (h->precision == GINT_FP32 || h->precision == GINT_BF16X3 || h->precision == GINT_FP16X3 ||
+        h->precision == GINT_FP16X4) {
         *fp32 = true;
         return GINT_OK;
     }
@@ -58,8 +65,8 @@ gint_status gint_vlocal(gint_handle* h, const double* V, double* H, int accumula
     if (!dg.ok) { set_error("cannot select device %d", h->device); return GINT_ERR_CUDA; }
     cudaStream_t st = (cudaStream_t)stream;
     if (!accumulate && h->n_values > 0) GINT_CUDA_TRY(cudaMemsetAsync(H, 0, sizeof(double) * h->n_values, st));
-    if (h->precision == GINT_BF16X3 || h->precision == GINT_FP16X3)
-        s = tc_vlocal(h, h->precision == GINT_BF16X3 ? 1 : 0, V, H, st);
+    if (is_tc(h))
+        s = tc_vlocal(h, tc_form(h), V, H, st);
     else
         s = simt_run(h, 0, fp32, V, nullptr, H, nullptr, nullptr, st);
     if (s != GINT_OK) return s;
@@ -75,8 +82,8 @@ gint_status gint_rho(gint_handle* h, const double* D, double* rho, gint_stream s
     DeviceGuard dg(h->device);
     if (!dg.ok) { set_error("cannot select device %d", h->device); return GINT_ERR_CUDA; }
     cudaStream_t st = (cudaStream_t)stream;
-    if (h->precision == GINT_BF16X3 || h->precision == GINT_FP16X3)
-        s = tc_rhoforce(h, h->precision == GINT_BF16X3 ? 1 : 0, false, nullptr, D, rho, nullptr, nullptr, st);
+    if (is_tc(h))
+        s = tc_rhoforce(h, tc_form(h), false, nullptr, D, rho, nullptr, nullptr, st);
     else
         s = simt_run(h, 1, fp32, nullptr, D, rho, nullptr, nullptr, st);
     if (s != GINT_OK) return s;
@@ -96,8 +103,8 @@ gint_status gint_force_stress(gint_handle* h, const double* V, const double* D, 
     cudaStream_t st = (cudaStream_t)stream;
     GINT_CUDA_TRY(cudaMemsetAsync(h->d_facc, 0, sizeof(double) * 12 * h->n_atoms, st));
     GINT_CUDA_TRY(cudaMemsetAsync(h->d_red, 0, sizeof(double), st));
-    if (h->precision == GINT_BF16X3 || h->precision == GINT_FP16X3)
-        s = tc_rhoforce(h, h->precision == GINT_BF16X3 ? 1 : 0, true, V, D, nullptr, h->d_facc, h->d_red, st);
+    if (is_tc(h))
+        s = tc_rhoforce(h, tc_form(h), true, V, D, nullptr, h->d_facc, h->d_red, st);
     else
         s = simt_run(h, 2, fp32, V, D, nullptr, h->d_facc, h->d_red, st);
     if (s != GINT_OK) return s;

@@ -23,6 +23,7 @@ struct SpeciesFast {
     int coef4;            // offset of the species' table in float4 units
     int rad_l[kMaxRadial];
     int orb_base[kMaxRadial];  // first orbital of each radial function
+    signed char qe[kMaxNw];    // fixed-point quantum exponent of each orbital (|phi| <= 127 * 2^qe)
 };
 
 __device__ __forceinline__ void species_fast_from(const SpeciesDev& s, SpeciesFast& f) {
@@ -34,6 +35,7 @@ __device__ __forceinline__ void species_fast_from(const SpeciesDev& s, SpeciesFa
     f.inv_dr = s.inv_dr_f;
     f.coef4 = (int)(s.tab_off >> 2);
     for (int j = 0; j < kMaxRadial; ++j) { f.rad_l[j] = j < s.n_radial ? s.rad_l[j] : 0; f.orb_base[j] = 0; }
+    for (int o = 0; o < kMaxNw; ++o) f.qe[o] = o < s.n_orb ? s.orb_qe[o] : 0;
     // orbital order: l ascending, radial functions in input order, m = -l..l
     int o = 0;
     for (int l = 0; l <= kMaxL; ++l)
@@ -123,6 +125,70 @@ __device__ __forceinline__ bool orbitals_fast(const SpeciesFast& s, const float4
                 a * s14 * dz + u * k3e * (xx - yy));
             put(o + 6, u * s15, a * s15 * dx + u * k3a * 3.f * (xx - yy), a * s15 * dy - u * k3a * 6.f * dx * dy,
                 a * s15 * dz);
+        }
+    }
+    return true;
+}
+
+}  // namespace gint
+
+namespace gint {
+
+// Orbital values of one atom image at two points: put2(o, v0, v1) for every
+// orbital o; a point outside the cutoff contributes 0.  Returns false (no
+// calls) when both points are outside.  Same functions as orbitals_fast.
+template <typename Put2>
+__device__ __forceinline__ bool orbitals_fast2(const SpeciesFast& s, const float4* __restrict__ coef, float ax,
+                                               float ay, float az, float bx, float by, float bz, Put2&& put2) {
+    const float r2a = ax * ax + ay * ay + az * az;
+    const float r2b = bx * bx + by * by + bz * bz;
+    const bool ina = r2a < s.rc2, inb = r2b < s.rc2;
+    if (!ina && !inb) return false;
+    // a point outside the cutoff is evaluated at a safe radius and multiplied by 0
+    const float ra = sqrtf(fminf(r2a, s.rc2 * 0.999f)), rb = sqrtf(fminf(r2b, s.rc2 * 0.999f));
+    const bool tinya = r2a < 1e-20f, tinyb = r2b < 1e-20f;
+    const float ia = tinya ? 0.f : 1.f / ra, ib = tinyb ? 0.f : 1.f / rb;
+    const float ma = ina ? 1.f : 0.f, mb = inb ? 1.f : 0.f;
+    const float xa = ra * s.inv_dr, xb = rb * s.inv_dr;
+    const int ka = min((int)xa, s.n_int - 1), kb = min((int)xb, s.n_int - 1);
+    const float ta = xa - (float)ka, tb = xb - (float)kb;
+    const float k00 = 0.28209479177387814f, k1 = 0.48860251190291992f;
+    const float k2a = 1.0925484305920792f, k2b = 0.31539156525252005f, k2c = 0.54627421529603959f;
+    const float k3a = 0.59004358992664352f, k3b = 2.8906114426405538f, k3c = 0.45704579946446572f;
+    const float k3d = 0.37317633259011540f, k3e = 1.4453057213202769f;
+    const float4* cfa = coef + s.coef4 + ka * s.n_radial;
+    const float4* cfb = coef + s.coef4 + kb * s.n_radial;
+    for (int j = 0; j < s.n_radial; ++j) {
+        const float4 ca = __ldg(cfa + j), cb = __ldg(cfb + j);
+        const int l = s.rad_l[j];
+        const int o = s.orb_base[j];
+        float ua = (ca.x + ta * (ca.y + ta * (ca.z + ta * ca.w))) * ma;
+        float ub = (cb.x + tb * (cb.y + tb * (cb.z + tb * cb.w))) * mb;
+        if (tinya) ua = (l == 0) ? ua : 0.f;  // centre limit: phi = R(0) Y00 for l = 0, 0 otherwise
+        if (tinyb) ub = (l == 0) ? ub : 0.f;
+        for (int q = 0; q < l; ++q) { ua *= ia; ub *= ib; }
+        if (l == 0) {
+            put2(o, ua * k00, ub * k00);
+        } else if (l == 1) {
+            put2(o + 0, ua * k1 * ay, ub * k1 * by);
+            put2(o + 1, ua * k1 * az, ub * k1 * bz);
+            put2(o + 2, ua * k1 * ax, ub * k1 * bx);
+        } else if (l == 2) {
+            put2(o + 0, ua * k2a * ax * ay, ub * k2a * bx * by);
+            put2(o + 1, ua * k2a * ay * az, ub * k2a * by * bz);
+            put2(o + 2, ua * k2b * (2.f * az * az - ax * ax - ay * ay), ub * k2b * (2.f * bz * bz - bx * bx - by * by));
+            put2(o + 3, ua * k2a * ax * az, ub * k2a * bx * bz);
+            put2(o + 4, ua * k2c * (ax * ax - ay * ay), ub * k2c * (bx * bx - by * by));
+        } else {
+            const float xxa = ax * ax, yya = ay * ay, zza = az * az, xxb = bx * bx, yyb = by * by, zzb = bz * bz;
+            const float qa = 4.f * zza - xxa - yya, qb = 4.f * zzb - xxb - yyb;
+            put2(o + 0, ua * k3a * ay * (3.f * xxa - yya), ub * k3a * by * (3.f * xxb - yyb));
+            put2(o + 1, ua * k3b * ax * ay * az, ub * k3b * bx * by * bz);
+            put2(o + 2, ua * k3c * ay * qa, ub * k3c * by * qb);
+            put2(o + 3, ua * k3d * az * (2.f * zza - 3.f * xxa - 3.f * yya), ub * k3d * bz * (2.f * zzb - 3.f * xxb - 3.f * yyb));
+            put2(o + 4, ua * k3c * ax * qa, ub * k3c * bx * qb);
+            put2(o + 5, ua * k3e * az * (xxa - yya), ub * k3e * bz * (xxb - yyb));
+            put2(o + 6, ua * k3a * ax * (xxa - 3.f * yya), ub * k3a * bx * (xxb - 3.f * yyb));
         }
     }
     return true;

@@ -40,6 +40,7 @@ struct SpeciesDev {
     signed char orb_rad[kMaxNw];  // radial function of each orbital
     signed char orb_l[kMaxNw];
     signed char orb_m[kMaxNw];    // m + l, 0..2l
+    signed char orb_qe[kMaxNw];   // |phi_o(r)| <= 127 * 2^orb_qe for every r (fixed-point quantum)
 };
 
 // An atom image (I, T) whose cutoff sphere meets the grid.

@@ -540,6 +540,21 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
                         ++norb;
                     }
         D.n_orb = norb;
+        // fixed-point quantum of each orbital: |R| on a knot interval is at most
+        // max |y| + (4/27) dr (|y'_k| + |y'_k+1|) (cubic Hermite basis bounds), and
+        // |Y_lm| <= sqrt((2l + 1) / 4 pi) (addition theorem); 0.1 % margin for FP32
+        for (int o = 0; o < norb; ++o) {
+            const gint_radial& R = S.radial[D.orb_rad[o]];
+            double bR = 0.0;
+            for (int k = 0; k + 1 < R.n_knots; ++k) {
+                const double dk = R.dy ? std::fabs(R.dy[k]) + std::fabs(R.dy[k + 1]) : 0.0;
+                bR = std::max(bR, std::max(std::fabs(R.y[k]), std::fabs(R.y[k + 1])) + (4.0 / 27.0) * R.dr * dk);
+            }
+            const double bound = 1.001 * bR * std::sqrt((2.0 * D.orb_l[o] + 1.0) / (4.0 * M_PI));
+            int e = 0;
+            if (bound > 0.0) std::frexp(bound / 127.0, &e);  // bound / 127 < 2^e
+            D.orb_qe[o] = (signed char)std::max(-100, std::min(100, e));
+        }
         nw_sp[s] = norb;
         rc_sp[s] = S.rc;
         max_nw = std::max(max_nw, norb);
@@ -845,7 +860,7 @@ gint_status gint_setup(int n_atoms, const double* pos, const int* species, const
             if (opt->reserved[i] != 0) { set_error("gint_options.reserved must be zero"); return GINT_ERR_INVALID_ARG; }
         for (int i = 0; i < 3; ++i)
             if (opt->brick[i] < 0 || opt->brick[i] > kMaxBrickPts) { set_error("brick[%d] out of range", i); return GINT_ERR_INVALID_ARG; }
-        if (opt->precision < GINT_FP64 || opt->precision > GINT_FP16X3) { set_error("unknown precision"); return GINT_ERR_INVALID_ARG; }
+        if (opt->precision < GINT_FP64 || opt->precision > GINT_FP16X4) { set_error("unknown precision"); return GINT_ERR_INVALID_ARG; }
     }
     int dev = (opt && opt->device >= 0) ? opt->device : -1;
     if (dev < 0) {
@@ -884,7 +899,7 @@ gint_status gint_pattern(const gint_handle* h, int64_t* n_blocks, int64_t* n_val
 
 gint_status gint_set_precision(gint_handle* h, int precision) {
     if (!h) { set_error("handle is NULL"); return GINT_ERR_INVALID_ARG; }
-    if (precision < GINT_FP64 || precision > GINT_FP16X3) { set_error("unknown precision %d", precision); return GINT_ERR_INVALID_ARG; }
+    if (precision < GINT_FP64 || precision > GINT_FP16X4) { set_error("unknown precision %d", precision); return GINT_ERR_INVALID_ARG; }
     h->precision = precision;
     return GINT_OK;
 }

@@ -16,6 +16,18 @@
 //     two chunk buffers alternate so orbital evaluation overlaps the MMAs;
 //   * after the last chunk the accumulators are read back (tcgen05.ld), scaled
 //     by 2^-s and added to the canonical H blocks with FP64 atomics.
+// Measured errors of the three-product form grow with the number of MMA
+// additions per element (96 per brick) the way a rounding biased towards zero
+// in the FP32 accumulator predicts, and the bias does not average out over the
+// bricks that add into one H element.  The exact form
+// (fp16x4) avoids that bias for the leading term: every operand value x of row
+// (orbital) o is written as x / q_o = n + l with q_o = 2^qe_o a per-orbital
+// quantum (|x| <= 127 q_o for every point), n = rint(x / q_o) an integer of at
+// most 8 bits and l = x / q_o - n in fp16.  Products n_a n_b are integers below
+// 2^14, so their sums over <= 1024 points stay below 2^24 and accumulate
+// exactly in FP32; the cross terms n l + l n + l l (2^-7 of the leading term)
+// go to a second accumulator.  Each output column then takes two TMEM columns,
+// so a pass holds 256 output columns instead of 512.
 // The atom-to-brick displacement is taken in FP64 once per (brick, atom) and
 // split into two FP32 words; in-brick offsets are FP32.
 #include <algorithm>
@@ -28,13 +40,15 @@
 
 namespace gint {
 
-constexpr int kTcThreads = 256;
+constexpr int kTcProdThreads = 512;   // 16 producer warps: two halves, one per chunk buffer
+constexpr int kTcHalf = kTcProdThreads / 2;
+constexpr int kTcThreads = kTcProdThreads + 32;  // + one MMA-issuing warp
 constexpr int kTcChunk = 16;        // points per K chunk (one MMA K step)
 constexpr int kTcMaxRows = 640;     // padded brick orbitals (5 tiles of 128)
 constexpr int kTcMaxAtoms = 64;     // atom images per brick
-constexpr int kTcMaxPairsPerPass = 4;
 constexpr int kTcMaxPts = 1024;     // points per brick on this path
 constexpr int kTcMaxSpecies = 8;
+constexpr int kTcMaxSeg = 16;       // (row tile, column range) segments per brick
 constexpr long kWaitLimit = 1L << 26;  // bounded mbarrier polls
 
 // bytes of one 16-bit operand piece for one chunk: rows x 16 points x 2 B
@@ -63,12 +77,22 @@ struct TcSmem {
     SpeciesFast spf[kTcMaxSpecies];
     unsigned char row_atom[kTcMaxRows];
     unsigned char row_mu[kTcMaxRows];
-    uint64_t bar[2];
+    unsigned short rowtab[kTcMaxRows];  // byte offset of row r's 16-byte segment in a piece
+    float row_q[kTcMaxRows];            // exact form: quantum 2^qe of row r
+    unsigned char seg_tile[kTcMaxSeg];  // segment: row tile, columns [c0, c1), TMEM column
+    short seg_c0[kTcMaxSeg], seg_c1[kTcMaxSeg], seg_tcol[kTcMaxSeg];
+    int pass_first[kTcMaxSeg + 1];      // first segment of each pass
+    int npass, nrow, ncol;
+    uint64_t full[2];   // producers of buffer b arrived (kTcHalf arrivals)
+    uint64_t empty[2];  // MMAs reading buffer b completed (tcgen05.commit)
+    uint64_t done;      // all MMAs of the pass completed
     uint32_t tmem;
     int work;
     int abort;
     float scale_inv;
 };
+
+static_assert(sizeof(TcSmem) + 1024 <= 232448, "shared memory of the H^V kernel exceeds 227 KB");
 
 // Offset (bytes) of element (row r, point q) of one piece: core matrix
 // (r / 8, q / 8) at ((r / 8) * 2 + q / 8) * 128, inside it row r % 8 of 16 bytes.
@@ -96,32 +120,49 @@ template <> struct Conv<__nv_bfloat16> {
     static constexpr int bf16 = 1;
 };
 
-template <typename H16>
+// Exact form: s = n + l with n = rint(s) (|s| <= 127.5, so n is exact in fp16) and l = s - n in fp16.
+__device__ __forceinline__ void fix_split(float s, unsigned short& hi, unsigned short& lo) {
+    const float n = rintf(s);
+    hi = __half_as_ushort(__float2half_rn(n));
+    lo = __half_as_ushort(__float2half_rn(s - n));
+}
+__device__ __forceinline__ float exp2i(int e) { return __int_as_float((127 + e) << 23); }  // 2^e, |e| < 127
+
+template <typename H16, bool kExact>
 __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const double* V, double* H) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
     const Problem& P = A.P;
     const GridDev& g = P.g;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t idesc = tc::idesc_f16(128, 128, Conv<H16>::bf16, 0, 0);
+    constexpr int kPassCols = kExact ? 256 : 512;  // output columns per pass
 
     if (warp == 0) {
         tc::tmem_alloc(&S.tmem, 512);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(&S.bar[0], 1);
-        tc::mbar_init(&S.bar[1], 1);
+        tc::mbar_init(&S.full[0], kTcHalf);
+        tc::mbar_init(&S.full[1], kTcHalf);
+        tc::mbar_init(&S.empty[0], 1);
+        tc::mbar_init(&S.empty[1], 1);
+        tc::mbar_init(&S.done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         S.abort = 0;
     }
     if (tid < P.n_species) species_fast_from(P.sp[tid], S.spf[tid]);
+    for (int r = tid; r < kTcMaxRows; r += kTcThreads) S.rowtab[r] = (unsigned short)((((r >> 3) * (kTcChunk / 8)) << 7) + ((r & 7) << 4));
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = S.tmem;
-    uint32_t commits[2] = {0, 0};  // completed-phase counters per buffer (same in every thread)
+    // completed phases of each barrier (every thread that waits on a barrier keeps its count)
+    uint32_t uses[2] = {0, 0};  // chunks produced into / issued from buffer b
+    uint32_t dones = 0;
     const float4* coef4 = reinterpret_cast<const float4*>(P.coef32);
+    const bool issuer_warp = warp == kTcProdThreads / 32;
+    const int half = warp >> 3;  // producer half (0 or 1) for warps 0-15
+    const int lt = tid & (kTcHalf - 1);
 
     for (;;) {
         if (tid == 0) S.work = atomicAdd(A.counter, 1);
@@ -162,7 +203,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
             q4.x = (float)l0 * (float)g.step[0][0] + (float)l1 * (float)g.step[1][0] + (float)l2 * (float)g.step[2][0];
             q4.y = (float)l0 * (float)g.step[0][1] + (float)l1 * (float)g.step[1][1] + (float)l2 * (float)g.step[2][1];
             q4.z = (float)l0 * (float)g.step[0][2] + (float)l1 * (float)g.step[1][2] + (float)l2 * (float)g.step[2][2];
-            q4.w = wv;
+            q4.w = p < g.bpts ? wv : 0.f;
             S.pt[p] = q4;
             wmax = fmaxf(wmax, fabsf(wv));
         }
@@ -179,16 +220,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
             int off = 0;
             for (int i = 0; i < na; ++i) {
                 S.at[i].off = off;
-                for (int o = 0; o < S.at[i].nw; ++o) { S.row_atom[off + o] = (unsigned char)i; S.row_mu[off + o] = (unsigned char)o; }
+                const SpeciesFast& sf = S.spf[S.at[i].sp];
+                for (int o = 0; o < S.at[i].nw; ++o) {
+                    S.row_atom[off + o] = (unsigned char)i;
+                    S.row_mu[off + o] = (unsigned char)o;
+                    if (kExact) S.row_q[off + o] = exp2i(sf.qe[o]);
+                }
                 off += S.at[i].nw;
             }
+            // row tiles of 128; tile i accumulates columns [128 i, ncol), cut into segments
+            // so that each pass holds at most kPassCols output columns (512 TMEM columns)
+            const int ncol = (off + 15) & ~15;
+            const int nt = (off + 127) >> 7;
+            int np = 0, used = 0, ns = 0;
+            S.pass_first[0] = 0;
+            for (int i = 0; i < nt; ++i) {
+                int c = 128 * i;
+                while (c < ncol) {
+                    if (used == kPassCols) { S.pass_first[++np] = ns; used = 0; }
+                    const int wdt = min(ncol - c, kPassCols - used);
+                    S.seg_tile[ns] = (unsigned char)i;
+                    S.seg_c0[ns] = (short)c;
+                    S.seg_c1[ns] = (short)(c + wdt);
+                    S.seg_tcol[ns] = (short)used;
+                    ++ns;
+                    used += wdt;
+                    c += wdt;
+                }
+            }
+            S.pass_first[++np] = ns;
+            S.npass = np;
+            S.nrow = off;
+            S.ncol = ncol;
         }
         __syncthreads();
         const float wscale = 1.f / S.scale_inv;
         for (int p = tid; p < g.bpad; p += kTcThreads) S.pt[p].w *= wscale;
-        int nrow = 0;
-        for (int i = 0; i < na; ++i) nrow += S.at[i].nw;
-        const int nt = (nrow + 127) >> 7;
+        const int nrow = S.nrow, npass = S.npass;
         // pair table: offsets of canonical blocks for pairs within cutoff
         for (int q = tid; q < na * na; q += kTcThreads) {
             const int a1 = q / na, a2 = q - a1 * na;
@@ -208,9 +276,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
             }
             S.pairoff[a1 * na + a2] = off;
         }
-        // zero the padding rows [nrow, nt*128) of both chunk buffers
+        // zero the padding rows [nrow, round128(nrow)) of both chunk buffers
+        const int nrow128 = (nrow + 127) & ~127;
         for (int b = 0; b < 2; ++b)
-            for (int e = tid; e < (nt * 128 - nrow) * kTcChunk; e += kTcThreads) {
+            for (int e = tid; e < (nrow128 - nrow) * kTcChunk; e += kTcThreads) {
                 const int r = nrow + e / kTcChunk, q = e % kTcChunk;
                 const int o = piece_off(r, q);
                 for (int pc = 0; pc < 4; ++pc)
@@ -218,144 +287,161 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
             }
         __syncthreads();
 
-        // ---- tile pairs (i <= j), processed in passes of up to four
-        const int npairs = nt * (nt + 1) / 2;
         const int nchunks = g.bpad / kTcChunk;
-        for (int pass0 = 0; pass0 < npairs && !S.abort; pass0 += kTcMaxPairsPerPass) {
-            const int pass_n = min(kTcMaxPairsPerPass, npairs - pass0);
-            // tiles whose rows this pass reads; only atom images with rows in them are produced
-            unsigned need = 0;
-            {
-                int pi = 0, pj = 0;
-                for (int t = 0; t < pass0 + pass_n; ++t) {
-                    if (t >= pass0) need |= (1u << pi) | (1u << pj);
-                    if (++pj >= nt) { ++pi; pj = pi; }
-                }
-            }
-            for (int c = 0; c < nchunks; ++c) {
-                const int b = c & 1;
-                // the MMAs of the chunk that last used this buffer must be done
-                if (commits[b] > 0) {
-                    if (!tc::mbar_wait(&S.bar[b], (commits[b] - 1) & 1, kWaitLimit)) {
-                        if (lane == 0) atomicOr(&S.abort, 1);
-                    }
-                }
-                // orbital values of the needed atom images at the chunk's 16 points
+        for (int pass = 0; pass < npass && !S.abort; ++pass) {
+            const int s0p = S.pass_first[pass], s1p = S.pass_first[pass + 1];
+            const int row_lo = 128 * S.seg_tile[s0p];  // rows below this are not read in this pass
+            if (!issuer_warp) {
+                // ---- producers: half h fills buffer h with chunks c = h, h + 2, ...
+                const int b = half;
                 unsigned char* buf = S.buf[b];
-                for (int item = tid; item < na * kTcChunk; item += kTcThreads) {
-                    const int a = item / kTcChunk, q = item - a * kTcChunk;
-                    const TcAtom& X = S.at[a];
-                    const int t0 = X.off >> 7, t1 = (X.off + X.nw - 1) >> 7;
-                    if (!((need >> t0) & 1u) && !((need >> t1) & 1u)) continue;
-                    const int p = c * kTcChunk + q;
-                    const float4 q4 = S.pt[p];
-                    const float dx = (X.c_hi[0] + q4.x) + X.c_lo[0];
-                    const float dy = (X.c_hi[1] + q4.y) + X.c_lo[1];
-                    const float dz = (X.c_hi[2] + q4.z) + X.c_lo[2];
-                    const float wv = q4.w;
-                    const int rbase = X.off;
-                    auto put = [&](int o, float v, float, float, float) {
-                        unsigned short ah, al, bh, bl;
-                        Conv<H16>::split(v * wv, ah, al);
-                        Conv<H16>::split(v, bh, bl);
-                        const int off = piece_off(rbase + o, q);
-                        *reinterpret_cast<unsigned short*>(&buf[0 * kPieceBytes + off]) = ah;
-                        *reinterpret_cast<unsigned short*>(&buf[1 * kPieceBytes + off]) = al;
-                        *reinterpret_cast<unsigned short*>(&buf[2 * kPieceBytes + off]) = bh;
-                        *reinterpret_cast<unsigned short*>(&buf[3 * kPieceBytes + off]) = bl;
-                    };
-                    const bool inside = p < g.bpts && orbitals_fast<false>(S.spf[X.sp], coef4, dx, dy, dz, put);
-                    if (!inside)
-                        for (int o = 0; o < X.nw; ++o) {
-                            const int off = piece_off(rbase + o, q);
-                            for (int pc = 0; pc < 4; ++pc) *reinterpret_cast<unsigned short*>(&buf[pc * kPieceBytes + off]) = 0;
-                        }
+                for (int c = b; c < nchunks; c += 2) {
+                    if (uses[b] > 0 && !S.abort && !tc::mbar_wait(&S.empty[b], (uses[b] - 1) & 1, kWaitLimit))
+                        atomicOr(&S.abort, 1);
+                    // orbital values at the chunk's points, two points per item, for atom
+                    // images with rows this pass reads
+                    for (int item = lt; item < na * (kTcChunk / 2); item += kTcHalf) {
+                        const int a = item / (kTcChunk / 2), qp = item - a * (kTcChunk / 2);
+                        const TcAtom& X = S.at[a];
+                        if (X.off + X.nw <= row_lo) continue;
+                        const int q = 2 * qp;
+                        const int p = c * kTcChunk + q;
+                        const float4 u4 = S.pt[p], v4 = S.pt[p + 1];
+                        const float ax = (X.c_hi[0] + u4.x) + X.c_lo[0];
+                        const float ay = (X.c_hi[1] + u4.y) + X.c_lo[1];
+                        const float az = (X.c_hi[2] + u4.z) + X.c_lo[2];
+                        const float bx = (X.c_hi[0] + v4.x) + X.c_lo[0];
+                        const float by = (X.c_hi[1] + v4.y) + X.c_lo[1];
+                        const float bz = (X.c_hi[2] + v4.z) + X.c_lo[2];
+                        const float wa = u4.w, wb = v4.w;  // zero at padding points
+                        const int qoff = ((q >> 3) << 7) + ((q & 7) << 1);
+                        const int rbase = X.off;
+                        const SpeciesFast& sf = S.spf[X.sp];
+                        auto put2 = [&](int o, float va, float vb) {
+                            unsigned short ah0, al0, bh0, bl0, ah1, al1, bh1, bl1;
+                            if (kExact) {
+                                const float qi = exp2i(-sf.qe[o]);
+                                va *= qi;
+                                vb *= qi;
+                                fix_split(va * wa, ah0, al0);
+                                fix_split(vb * wb, ah1, al1);
+                                fix_split(va, bh0, bl0);
+                                fix_split(vb, bh1, bl1);
+                            } else {
+                                Conv<H16>::split(va * wa, ah0, al0);
+                                Conv<H16>::split(vb * wb, ah1, al1);
+                                Conv<H16>::split(va, bh0, bl0);
+                                Conv<H16>::split(vb, bh1, bl1);
+                            }
+                            const int off = S.rowtab[rbase + o] + qoff;
+                            *reinterpret_cast<uint32_t*>(&buf[0 * kPieceBytes + off]) = ah0 | ((uint32_t)ah1 << 16);
+                            *reinterpret_cast<uint32_t*>(&buf[1 * kPieceBytes + off]) = al0 | ((uint32_t)al1 << 16);
+                            *reinterpret_cast<uint32_t*>(&buf[2 * kPieceBytes + off]) = bh0 | ((uint32_t)bh1 << 16);
+                            *reinterpret_cast<uint32_t*>(&buf[3 * kPieceBytes + off]) = bl0 | ((uint32_t)bl1 << 16);
+                        };
+                        if (!orbitals_fast2(sf, coef4, ax, ay, az, bx, by, bz, put2))
+                            for (int o = 0; o < X.nw; ++o) {
+                                const int off = S.rowtab[rbase + o] + qoff;
+                                for (int pc = 0; pc < 4; ++pc) *reinterpret_cast<uint32_t*>(&buf[pc * kPieceBytes + off]) = 0u;
+                            }
+                    }
+                    tc::fence_async_smem();
+                    tc::mbar_arrive(&S.full[b]);
+                    uses[b] += 1;
                 }
-                tc::fence_async_smem();
-                __syncthreads();
-                if (S.abort) break;
-                if (tid == 0) {
+            } else if (lane == 0) {
+                // ---- issuer: one thread waits for each chunk, issues its MMAs and commits
+                const uint32_t lbo = 128, sbo = (kTcChunk / 8) * 128;
+                for (int c = 0; c < nchunks; ++c) {
+                    const int b = c & 1;
+                    if (!S.abort && !tc::mbar_wait(&S.full[b], uses[b] & 1, kWaitLimit)) atomicOr(&S.abort, 1);
+                    uses[b] += 1;
                     tc::fence_after_sync();
-                    const uint32_t base = tc::smem_u32(buf);
+                    const uint32_t base = tc::smem_u32(S.buf[b]);
                     // K-major operands: LBO = distance of K-adjacent core matrices (128 B),
                     // SBO = distance of row-adjacent core matrices (2 * 128 B)
-                    const uint32_t lbo = 128, sbo = (kTcChunk / 8) * 128;
-                    int pi = 0, pj = 0, k = 0;
-                    for (int t = 0; t < pass0 + pass_n; ++t) {
-                        if (t >= pass0) {
-                            const uint32_t tile_bytes = 128 * kTcChunk * 2;  // 16 row groups
-                            const uint32_t a_hi = base + 0 * kPieceBytes + pi * tile_bytes;
-                            const uint32_t a_lo = base + 1 * kPieceBytes + pi * tile_bytes;
-                            const uint32_t b_hi = base + 2 * kPieceBytes + pj * tile_bytes;
-                            const uint32_t b_lo = base + 3 * kPieceBytes + pj * tile_bytes;
-                            const uint32_t d = tmem + (uint32_t)((t - pass0) * 128);
-                            tc::mma_f16(d, tc::smem_desc(a_hi, lbo, sbo), tc::smem_desc(b_hi, lbo, sbo), idesc, c > 0 ? 1u : 0u);
-                            tc::mma_f16(d, tc::smem_desc(a_hi, lbo, sbo), tc::smem_desc(b_lo, lbo, sbo), idesc, 1u);
-                            tc::mma_f16(d, tc::smem_desc(a_lo, lbo, sbo), tc::smem_desc(b_hi, lbo, sbo), idesc, 1u);
-                        }
-                        // next pair (i, j), i <= j, row-major over the upper triangle
-                        ++k;
-                        if (++pj >= nt) { ++pi; pj = pi; }
-                    }
-                    (void)k;
-                    tc::mma_commit(&S.bar[b]);
-                }
-                commits[b] += 1;
-            }
-            // ---- wait for the last chunk's MMAs (the commit covers all earlier ones)
-            {
-                const int bl = (nchunks - 1) & 1;
-                if (!tc::mbar_wait(&S.bar[bl], (commits[bl] - 1) & 1, kWaitLimit)) {
-                    if (lane == 0) atomicOr(&S.abort, 1);
-                }
-                const int bo = bl ^ 1;
-                if (commits[bo] > 0 && !tc::mbar_wait(&S.bar[bo], (commits[bo] - 1) & 1, kWaitLimit)) {
-                    if (lane == 0) atomicOr(&S.abort, 1);
-                }
-            }
-            tc::fence_after_sync();
-            __syncthreads();
-            if (S.abort) break;
-            // ---- epilogue: warps 0-3 columns 0-63, warps 4-7 columns 64-127 of every tile of the pass
-            {
-                const int lane_base = (warp & 3) * 32;
-                const int col0 = (warp >> 2) * 64;
-                const float sinv = S.scale_inv;
-                int pi = 0, pj = 0;
-                for (int t = 0; t < pass0 + pass_n; ++t) {
-                    if (t >= pass0) {
-                        const int r = pi * 128 + lane_base + lane;
-                        const bool rvalid = r < nrow;
-                        const int a1 = rvalid ? S.row_atom[r] : 0;
-                        const int mu = rvalid ? S.row_mu[r] : 0;
-                        for (int cc = 0; cc < 64; cc += 16) {
-                            float v[16];
-                            tc::tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)((t - pass0) * 128 + col0 + cc), v);
-                            if (!rvalid) continue;
-#pragma unroll
-                            for (int jj = 0; jj < 16; ++jj) {
-                                const int col = pj * 128 + col0 + cc + jj;
-                                if (col >= nrow) continue;
-                                const int a2 = S.row_atom[col];
-                                if (a1 > a2) continue;
-                                const int64_t off = S.pairoff[a1 * na + a2];
-                                if (off < 0) continue;
-                                const int nu = S.row_mu[col];
-                                const double val = (double)(v[jj] * sinv);  // sinv is a power of two: exact
-                                const int nw2 = S.at[a2].nw;
-                                if (a1 == a2) {
-                                    // same atom image: the block is symmetric; the tile grid only holds
-                                    // r <= col for rows and columns in different tiles
-                                    if (r > col) continue;
-                                    atomicAdd(H + off + mu * nw2 + nu, val);
-                                    if (mu != nu) atomicAdd(H + off + nu * nw2 + mu, val);
+                    if (!S.abort) {
+                        for (int sg = s0p; sg < s1p; ++sg) {
+                            const int i = S.seg_tile[sg], c_end = S.seg_c1[sg];
+                            const uint32_t a_hi = base + 0 * kPieceBytes + (uint32_t)(i * 16) * sbo;
+                            const uint32_t a_lo = base + 1 * kPieceBytes + (uint32_t)(i * 16) * sbo;
+                            for (int c0 = S.seg_c0[sg]; c0 < c_end; c0 += 256) {
+                                const int nn = min(256, c_end - c0);
+                                const uint32_t idesc = tc::idesc_f16(128, nn, Conv<H16>::bf16, 0, 0);
+                                const uint32_t b_hi = base + 2 * kPieceBytes + (uint32_t)(c0 >> 3) * sbo;
+                                const uint32_t b_lo = base + 3 * kPieceBytes + (uint32_t)(c0 >> 3) * sbo;
+                                const uint32_t d = tmem + (uint32_t)(S.seg_tcol[sg] + c0 - S.seg_c0[sg]);
+                                tc::mma_f16(d, tc::smem_desc(a_hi, lbo, sbo), tc::smem_desc(b_hi, lbo, sbo), idesc, c > 0 ? 1u : 0u);
+                                if (kExact) {
+                                    // integer products alone in d; the cross terms in d + 256
+                                    const uint32_t d1 = d + 256;
+                                    tc::mma_f16(d1, tc::smem_desc(a_hi, lbo, sbo), tc::smem_desc(b_lo, lbo, sbo), idesc, c > 0 ? 1u : 0u);
+                                    tc::mma_f16(d1, tc::smem_desc(a_lo, lbo, sbo), tc::smem_desc(b_hi, lbo, sbo), idesc, 1u);
+                                    tc::mma_f16(d1, tc::smem_desc(a_lo, lbo, sbo), tc::smem_desc(b_lo, lbo, sbo), idesc, 1u);
                                 } else {
-                                    atomicAdd(H + off + mu * nw2 + nu, val);
+                                    tc::mma_f16(d, tc::smem_desc(a_hi, lbo, sbo), tc::smem_desc(b_lo, lbo, sbo), idesc, 1u);
+                                    tc::mma_f16(d, tc::smem_desc(a_lo, lbo, sbo), tc::smem_desc(b_hi, lbo, sbo), idesc, 1u);
                                 }
                             }
                         }
                     }
-                    if (++pj >= nt) { ++pi; pj = pi; }
+                    tc::mma_commit(&S.empty[b]);
+                }
+                tc::mma_commit(&S.done);
+            }
+            // ---- every thread: all MMAs of the pass complete
+            __syncwarp();
+            if (!S.abort && !tc::mbar_wait(&S.done, dones & 1, kWaitLimit)) atomicOr(&S.abort, 1);
+            dones += 1;
+            if (issuer_warp && lane != 0) {
+                // lanes 1-31 of the issuer warp keep the buffer counters in step with lane 0
+                for (int c = 0; c < nchunks; ++c) uses[c & 1] += 1;
+            }
+            tc::fence_after_sync();
+            __syncthreads();
+            if (S.abort) break;
+            // ---- epilogue: producer warps; lanes = rows (lane group warp & 3), the four warps of a
+            //      lane group take every fourth 16-column group
+            if (!issuer_warp) {
+                const int lane_base = (warp & 3) * 32;
+                const float sinv = S.scale_inv;
+                for (int sg = s0p; sg < s1p; ++sg) {
+                    const int i = S.seg_tile[sg], cs0 = S.seg_c0[sg];
+                    const int r = 128 * i + lane_base + lane;
+                    const bool rvalid = r < nrow;
+                    const int a1 = rvalid ? S.row_atom[r] : 0;
+                    const int mu = rvalid ? S.row_mu[r] : 0;
+                    const int ngrp = (S.seg_c1[sg] - cs0) >> 4;
+                    const float qr = kExact && rvalid ? S.row_q[r] * sinv : sinv;
+                    for (int gq = warp >> 2; gq < ngrp; gq += 4) {
+                        float v[16], v1[16];
+                        const uint32_t ta = tmem + ((uint32_t)lane_base << 16) + (uint32_t)(S.seg_tcol[sg] + 16 * gq);
+                        tc::tmem_ld16(ta, v);
+                        if (kExact) tc::tmem_ld16(ta + 256, v1);
+                        if (!rvalid) continue;
+#pragma unroll
+                        for (int jj = 0; jj < 16; ++jj) {
+                            const int col = cs0 + 16 * gq + jj;
+                            if (col >= nrow) continue;
+                            const int a2 = S.row_atom[col];
+                            if (a1 > a2) continue;
+                            const int64_t off = S.pairoff[a1 * na + a2];
+                            if (off < 0) continue;
+                            const int nu = S.row_mu[col];
+                            // scale factors are powers of two: exact
+                            const double val = kExact ? ((double)v[jj] + (double)v1[jj]) * (double)(qr * S.row_q[col])
+                                                      : (double)(v[jj] * sinv);
+                            const int nw2 = S.at[a2].nw;
+                            if (a1 == a2) {
+                                // same atom image: the block is symmetric; keep r <= col and mirror
+                                if (r > col) continue;
+                                atomicAdd(H + off + mu * nw2 + nu, val);
+                                if (mu != nu) atomicAdd(H + off + nu * nw2 + mu, val);
+                            } else {
+                                atomicAdd(H + off + mu * nw2 + nu, val);
+                            }
+                        }
+                    }
                 }
             }
             tc::fence_before_sync();
@@ -363,10 +449,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
         }
         __syncthreads();
     }
-    // ---- teardown: wait (bounded) for any MMA still in flight, then free TMEM
+    // ---- teardown: one more commit and a bounded wait, so that no MMA is in flight when
+    //      tensor memory is released (every pass already waited on `done` unless it aborted)
     __syncthreads();
-    for (int b = 0; b < 2; ++b)
-        if (commits[b] > 0) (void)tc::mbar_wait(&S.bar[b], (commits[b] - 1) & 1, kWaitLimit);
+    if (issuer_warp && lane == 0) tc::mma_commit(&S.done);
+    (void)tc::mbar_wait(&S.done, dones & 1, kWaitLimit);
     if (S.abort && tid == 0) atomicOr(P.err, kErrTimeout);
     tc::fence_before_sync();
     __syncthreads();
@@ -375,7 +462,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
 
 size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
 
-gint_status tc_vlocal(gint_handle* h, int bf16, const double* V, double* H, cudaStream_t st) {
+// form: 0 = fp16x3, 1 = bf16x3, 2 = fp16x4 (exact leading term)
+gint_status tc_vlocal(gint_handle* h, int form, const double* V, double* H, cudaStream_t st) {
     if (h->n_work == 0) return GINT_OK;
     if (h->max_brick_orb > kTcMaxRows || h->max_brick_atoms > kTcMaxAtoms || h->grid.bpad > kTcMaxPts ||
         h->grid.bpad % kTcChunk != 0 || h->n_species > kTcMaxSpecies) {
@@ -389,13 +477,16 @@ gint_status tc_vlocal(gint_handle* h, int bf16, const double* V, double* H, cuda
     A.counter = h->d_err + 2;
     GINT_CUDA_TRY(cudaMemsetAsync(A.counter, 0, sizeof(int), st));
     const size_t smem = tc_smem_bytes();
-    if (bf16) {
-        GINT_CUDA_TRY(cudaFuncSetAttribute(k_vlocal_tc<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_vlocal_tc<__nv_bfloat16><<<h->sm_count, kTcThreads, smem, st>>>(A, V, H);
-    } else {
-        GINT_CUDA_TRY(cudaFuncSetAttribute(k_vlocal_tc<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_vlocal_tc<__half><<<h->sm_count, kTcThreads, smem, st>>>(A, V, H);
-    }
+#define GINT_LAUNCH_VL(H16, X)                                                                                 \
+    do {                                                                                                       \
+        GINT_CUDA_TRY(cudaFuncSetAttribute(k_vlocal_tc<H16, X>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                           (int)smem));                                                        \
+        k_vlocal_tc<H16, X><<<h->sm_count, kTcThreads, smem, st>>>(A, V, H);                                   \
+    } while (0)
+    if (form == 1) GINT_LAUNCH_VL(__nv_bfloat16, false);
+    else if (form == 2) GINT_LAUNCH_VL(__half, true);
+    else GINT_LAUNCH_VL(__half, false);
+#undef GINT_LAUNCH_VL
     GINT_CUDA_TRY(cudaGetLastError());
     return GINT_OK;
 }

@@ -8,8 +8,9 @@
 //     listed; their orbitals are packed densely as the N dimension
 //     (<= 512 TMEM columns);
 //   * the K dimension runs over active atom images, one MMA K-step (16) per
-//     image (nw <= 16 orbitals, zero padded): A = Psi restricted to that
-//     image (128 points x 16), B = the image's D blocks against every active
+//     image (nw <= 16 orbitals, zero padded), two images per synchronisation:
+//     A = Psi restricted to that image (128 points x 16), B = the image's D
+//     blocks against every active
 //     image, copied row by row from a per-call pre-formatted copy of D
 //     (every pattern block as a 16 x 16 tile of hi/lo 16-bit pieces in
 //     K-major core-matrix order), so a B row is two 16-byte copies per piece;
@@ -46,14 +47,15 @@ struct Atom {
 };
 
 struct Smem {
-    unsigned char A[2][2 * kAPiece];   // [buffer][hi | lo]
-    unsigned char B[2][2 * kBPiece];
+    unsigned char A[2][2][2 * kAPiece];   // [buffer][image of the step][hi | lo]
+    unsigned char B[2][2][2 * kBPiece];
     Atom at[kMaxAtoms];
     int pairblk[kMaxAtoms * kMaxAtoms];  // block (I_a2, I_a1, T_a1 - T_a2) for K image a1, N image a2; -1 if none
     float W2[kMaxBrickPts];              // 2 V dV (force)
     double red[kMaxAtoms][13];           // per-image F(3), virial(9), energy
-    float Gst[4][32][17];                // epilogue: G values of one image per lane (padded row)
+    float Gst[8][32][17];                // epilogue: G values of one image per lane (padded row)
     float rho_part[128];                 // rho of the tile's points over earlier column groups
+    float rho_half[128];                 // partial rho from warps 4-7
     SpeciesFast spf[kMaxSpecies];
     unsigned char act[kMaxAtoms];
     int rowoff[kMaxAtoms + 1];
@@ -62,6 +64,8 @@ struct Smem {
     uint32_t tmem;
     int work, abort, nact, ncols;
 };
+
+static_assert(sizeof(Smem) + 1024 <= 232448, "shared memory of the rho/force kernel exceeds 227 KB");
 
 template <typename H16> struct Split;
 template <> struct Split<__half> {
@@ -261,80 +265,87 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
             for (int e = tid; e < (ncols - nrows) * 2; e += kThreads) {
                 const int r = nrows + (e >> 1), half = e & 1;
                 for (int b = 0; b < 2; ++b)
-                    for (int pc = 0; pc < 2; ++pc)
-                        *reinterpret_cast<uint4*>(&S.B[b][pc * kBPiece + kmaj16(r, half * 8)]) = make_uint4(0, 0, 0, 0);
+                    for (int j = 0; j < 2; ++j)
+                        for (int pc = 0; pc < 2; ++pc)
+                            *reinterpret_cast<uint4*>(&S.B[b][j][pc * kBPiece + kmaj16(r, half * 8)]) = make_uint4(0, 0, 0, 0);
             }
-            // ---- K loop over active images
-            for (int k = 0; k < nact; ++k, ++chunk) {
+            // ---- K loop over active images, two images (K = 32) per step
+            for (int k = 0; k < nact; k += 2, ++chunk) {
                 const int b = chunk & 1;
+                const int nk = min(2, nact - k);
                 if (commits[b] > 0 && !tc::mbar_wait(&S.bar[b], (commits[b] - 1) & 1, kWait))
                     if (lane == 0) atomicOr(&S.abort, 1);
-                const int a1 = S.act[k];
-                const Atom& X = S.at[a1];
-                if (tid < 128) {
-                    // A row p: orbital values of image a1 at point p (16 slots, zero padded)
-                    const int p = mt * 128 + tid;
-                    unsigned char* A0 = S.A[b];
-                    for (int o = X.nw; o < 16; ++o) {
-                        *reinterpret_cast<unsigned short*>(A0 + kmaj16(tid, o)) = 0;
-                        *reinterpret_cast<unsigned short*>(A0 + kAPiece + kmaj16(tid, o)) = 0;
+                // B rows (asynchronous copies first): for image a1 = act[k + j] and every active
+                // image a2 of the group, rows nu of block (I_a2, I_a1, T_a1 - T_a2)
+                for (int e = tid; e < nk * nrows * 4; e += kThreads) {
+                    const int j = e / (nrows * 4), rem = e - j * nrows * 4;
+                    const int r = rem >> 2, part = rem & 3;  // part: (piece, half)
+                    int lo_j = cg0, hi_j = cg1 - 1;
+                    while (lo_j < hi_j) {
+                        const int mid = (lo_j + hi_j + 1) >> 1;
+                        if (S.rowoff[mid] <= rbase + r) lo_j = mid; else hi_j = mid - 1;
                     }
-                    bool inside = false;
-                    if (p < g.bpts) {
-                        float fx, fy, fz;
-                        point_offset(g, p, fx, fy, fz);
-                        const float dx = (X.c_hi[0] + fx) + X.c_lo[0];
-                        const float dy = (X.c_hi[1] + fy) + X.c_lo[1];
-                        const float dz = (X.c_hi[2] + fz) + X.c_lo[2];
-                        auto put = [&](int o, float v, float, float, float) {
-                            unsigned short hi, lo;
-                            Split<H16>::run(v, hi, lo);
-                            *reinterpret_cast<unsigned short*>(A0 + kmaj16(tid, o)) = hi;
-                            *reinterpret_cast<unsigned short*>(A0 + kAPiece + kmaj16(tid, o)) = lo;
-                        };
-                        inside = orbitals_fast<false>(S.spf[X.sp], coef4, dx, dy, dz, put);
-                    }
-                    if (!inside)
-                        for (int o = 0; o < X.nw; ++o) {
-                            *reinterpret_cast<unsigned short*>(A0 + kmaj16(tid, o)) = 0;
-                            *reinterpret_cast<unsigned short*>(A0 + kAPiece + kmaj16(tid, o)) = 0;
+                    const int a2 = S.act[lo_j];
+                    const int nu = rbase + r - S.rowoff[lo_j];
+                    const int blk = S.pairblk[S.act[k + j] * na + a2];
+                    const int pc = part >> 1, half = part & 1;
+                    unsigned char* dst = &S.B[b][j][pc * kBPiece + kmaj16(r, half * 8)];
+                    if (blk >= 0) tc::cp_async16(dst, Dt + (int64_t)blk * 1024 + pc * 512 + kmaj16(nu, half * 8));
+                    else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
+                }
+                // A rows: orbital values of image act[k + j] at point p (16 slots, zero padded)
+                {
+                    const int j = tid >> 7, pl = tid & 127;
+                    if (j < nk) {
+                        const Atom& X = S.at[S.act[k + j]];
+                        const int p = mt * 128 + pl;
+                        unsigned char* A0 = S.A[b][j];
+                        for (int o = X.nw; o < 16; ++o) {
+                            *reinterpret_cast<unsigned short*>(A0 + kmaj16(pl, o)) = 0;
+                            *reinterpret_cast<unsigned short*>(A0 + kAPiece + kmaj16(pl, o)) = 0;
                         }
-                } else {
-                    // B rows: for every active image a2, rows nu of block (I_a2, I_a1, T_a1 - T_a2)
-                    const int t2 = tid - 128;
-                    for (int e = t2; e < nrows * 4; e += 128) {
-                        const int r = e >> 2, part = e & 3;  // part: (piece, half)
-                        // image of row r: largest j in the group with rowoff[j] <= rbase + r
-                        int lo_j = cg0, hi_j = cg1 - 1;
-                        while (lo_j < hi_j) {
-                            const int mid = (lo_j + hi_j + 1) >> 1;
-                            if (S.rowoff[mid] <= rbase + r) lo_j = mid; else hi_j = mid - 1;
+                        bool inside = false;
+                        if (p < g.bpts) {
+                            float fx, fy, fz;
+                            point_offset(g, p, fx, fy, fz);
+                            const float dx = (X.c_hi[0] + fx) + X.c_lo[0];
+                            const float dy = (X.c_hi[1] + fy) + X.c_lo[1];
+                            const float dz = (X.c_hi[2] + fz) + X.c_lo[2];
+                            auto put = [&](int o, float v, float, float, float) {
+                                unsigned short hi, lo;
+                                Split<H16>::run(v, hi, lo);
+                                *reinterpret_cast<unsigned short*>(A0 + kmaj16(pl, o)) = hi;
+                                *reinterpret_cast<unsigned short*>(A0 + kAPiece + kmaj16(pl, o)) = lo;
+                            };
+                            inside = orbitals_fast<false>(S.spf[X.sp], coef4, dx, dy, dz, put);
                         }
-                        const int a2 = S.act[lo_j];
-                        const int nu = rbase + r - S.rowoff[lo_j];
-                        const int blk = S.pairblk[a1 * na + a2];
-                        const int pc = part >> 1, half = part & 1;
-                        uint4 v = make_uint4(0, 0, 0, 0);
-                        if (blk >= 0) v = __ldg(reinterpret_cast<const uint4*>(Dt + (int64_t)blk * 1024 + pc * 512 + kmaj16(nu, half * 8)));
-                        *reinterpret_cast<uint4*>(&S.B[b][pc * kBPiece + kmaj16(r, half * 8)]) = v;
+                        if (!inside)
+                            for (int o = 0; o < X.nw; ++o) {
+                                *reinterpret_cast<unsigned short*>(A0 + kmaj16(pl, o)) = 0;
+                                *reinterpret_cast<unsigned short*>(A0 + kAPiece + kmaj16(pl, o)) = 0;
+                            }
                     }
                 }
+                tc::cp_async_wait_all();
                 tc::fence_async_smem();
                 __syncthreads();
                 if (S.abort) break;
                 if (tid == 0) {
                     tc::fence_after_sync();
-                    const uint32_t a_hi = tc::smem_u32(S.A[b]), a_lo = a_hi + kAPiece;
-                    const uint32_t bb = tc::smem_u32(S.B[b]);
-                    for (int n0 = 0; n0 < ncols; n0 += 256) {
-                        const int nn = min(256, ncols - n0);
-                        const uint32_t idesc = tc::idesc_f16(128, nn, Split<H16>::bf16, 0, 0);
-                        const uint32_t b_hi = bb + (n0 >> 3) * 256, b_lo = b_hi + kBPiece;
-                        const uint32_t d = tmem + (uint32_t)n0;
-                        // K-major, 16 K-columns: LBO (K-adjacent cores) 128 B, SBO (row groups) 256 B
-                        tc::mma_f16(d, tc::smem_desc(a_hi, 128, 256), tc::smem_desc(b_hi, 128, 256), idesc, k > 0 ? 1u : 0u);
-                        tc::mma_f16(d, tc::smem_desc(a_hi, 128, 256), tc::smem_desc(b_lo, 128, 256), idesc, 1u);
-                        tc::mma_f16(d, tc::smem_desc(a_lo, 128, 256), tc::smem_desc(b_hi, 128, 256), idesc, 1u);
+                    for (int j = 0; j < nk; ++j) {
+                        const uint32_t a_hi = tc::smem_u32(S.A[b][j]), a_lo = a_hi + kAPiece;
+                        const uint32_t bb = tc::smem_u32(S.B[b][j]);
+                        for (int n0 = 0; n0 < ncols; n0 += 256) {
+                            const int nn = min(256, ncols - n0);
+                            const uint32_t idesc = tc::idesc_f16(128, nn, Split<H16>::bf16, 0, 0);
+                            const uint32_t b_hi = bb + (n0 >> 3) * 256, b_lo = b_hi + kBPiece;
+                            const uint32_t d = tmem + (uint32_t)n0;
+                            // K-major, 16 K-columns: LBO (K-adjacent cores) 128 B, SBO (row groups) 256 B
+                            tc::mma_f16(d, tc::smem_desc(a_hi, 128, 256), tc::smem_desc(b_hi, 128, 256), idesc,
+                                        (k + j) > 0 ? 1u : 0u);
+                            tc::mma_f16(d, tc::smem_desc(a_hi, 128, 256), tc::smem_desc(b_lo, 128, 256), idesc, 1u);
+                            tc::mma_f16(d, tc::smem_desc(a_lo, 128, 256), tc::smem_desc(b_hi, 128, 256), idesc, 1u);
+                        }
                     }
                     tc::mma_commit(&S.bar[b]);
                 }
@@ -350,22 +361,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
             }
             __syncthreads();
             if (S.abort) break;
-            // ---- epilogue: warps 0-3, lane = point
-            if (warp < 4) {
-                const int p = mt * 128 + tid;
+            // ---- epilogue: lane = point (TMEM lane 32 (warp & 3) + lane); warps w and w + 4
+            //      take alternate atom images of the group
+            {
+                const int pl = (warp & 3) * 32 + lane;  // point within the tile
+                const int p = mt * 128 + pl;
                 int g0 = 0, g1 = 0, g2 = 0;
                 const bool pv = brick_point(g, b0, b1, b2, p, g0, g1, g2);
                 float fx = 0.f, fy = 0.f, fz = 0.f;
                 if (p < g.bpts) point_offset(g, p, fx, fy, fz);
-                float rho_p = cg0 == 0 ? 0.f : S.rho_part[tid];
-                for (int j = cg0; j < cg1; ++j) {
+                float rho_p = (cg0 == 0 || warp >= 4) ? 0.f : S.rho_part[pl];
+                for (int j = cg0 + (warp >> 2); j < cg1; j += 2) {
                     const int a2 = S.act[j];
                     const Atom& Y = S.at[a2];
                     int c0 = S.rowoff[j] - rbase;
                     int sh = 0;
                     if (c0 + 16 > kMaxCols) { sh = c0 + 16 - kMaxCols; c0 -= sh; }
                     float Gv[16];
-                    tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, Gv);
+                    tc::tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, Gv);
                     float* gs = S.Gst[warp][lane];
 #pragma unroll
                     for (int o = 0; o < 16; ++o) gs[o] = Gv[o];
@@ -398,10 +411,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
                             for (int q = 0; q < 13; ++q) atomicAdd(&S.red[j][q], (double)v[q]);
                     }
                 }
-                S.rho_part[tid] = rho_p;
-                if (!kForce && pv && cg1 == nact) rho[((int64_t)g0 * g.n[1] + g1) * g.n[2] + g2] = (double)rho_p;
+                if (warp >= 4) S.rho_half[pl] = rho_p;
+                tc::fence_before_sync();
+                __syncthreads();
+                if (warp < 4) {
+                    rho_p += S.rho_half[pl];
+                    S.rho_part[pl] = rho_p;
+                    if (!kForce && pv && cg1 == nact) rho[((int64_t)g0 * g.n[1] + g1) * g.n[2] + g2] = (double)rho_p;
+                }
             }
-            tc::fence_before_sync();
             __syncthreads();
             if (kForce) {
                 for (int e = tid; e < nact * 13; e += kThreads) {
@@ -433,6 +451,16 @@ static gint_status ensure_dt(gint_handle* h) {
     const size_t bytes = (size_t)std::max<int64_t>(1, h->n_blocks) * 1024;
     GINT_CUDA_TRY(cudaMalloc(&h->d_dt, bytes));
     return GINT_OK;
+}
+
+// Allocations the tensor-core calls make on first use, done ahead of a graph capture.
+gint_status tc_prepare(gint_handle* h) {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    gint_status s = ensure_dt(h);
+    if (prev >= 0) cudaSetDevice(prev);
+    return s;
 }
 
 gint_status tc_rhoforce(gint_handle* h, int bf16, bool force, const double* V, const double* D, double* rho,

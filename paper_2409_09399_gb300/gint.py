@@ -14,16 +14,16 @@ import numpy as np
 
 from . import _build
 
-GINT_FP64, GINT_FP32, GINT_TF32, GINT_BF16X3, GINT_BF16X6, GINT_FP16X3 = range(6)
+GINT_FP64, GINT_FP32, GINT_TF32, GINT_BF16X3, GINT_BF16X6, GINT_FP16X3, GINT_FP16X4 = range(7)
 PRECISIONS = {"fp64": GINT_FP64, "fp32": GINT_FP32, "tf32": GINT_TF32, "bf16x3": GINT_BF16X3,
-              "bf16x6": GINT_BF16X6, "fp16x3": GINT_FP16X3}
+              "bf16x6": GINT_BF16X6, "fp16x3": GINT_FP16X3, "fp16x4": GINT_FP16X4}
 STATUS = {0: "GINT_OK", 1: "GINT_ERR_INVALID_ARG", 2: "GINT_ERR_CUDA", 3: "GINT_ERR_OOM",
           4: "GINT_ERR_PATTERN_MISMATCH", 5: "GINT_ERR_TIMEOUT", 6: "GINT_ERR_UNSUPPORTED", 7: "GINT_ERR_DEVICE"}
 
 # exported symbols, in the order include/gint.h declares them
 SYMBOLS = ["gint_setup", "gint_destroy", "gint_pattern", "gint_set_precision", "gint_vlocal", "gint_rho",
-           "gint_force_stress", "gint_vlocal_static", "gint_sync", "gint_get_info", "gint_work_stats",
-           "gint_last_error"]
+           "gint_force_stress", "gint_vlocal_static", "gint_batch_create", "gint_batch_run",
+           "gint_batch_destroy", "gint_sync", "gint_get_info", "gint_work_stats", "gint_last_error"]
 
 
 class GintError(RuntimeError):
@@ -84,6 +84,12 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.gint_force_stress.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     L.gint_vlocal_static.restype = i32
     L.gint_vlocal_static.argtypes = [vp, vp, vp, vp]
+    L.gint_batch_create.restype = i32
+    L.gint_batch_create.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.gint_batch_run.restype = i32
+    L.gint_batch_run.argtypes = [vp] + [ctypes.POINTER(vp)] * 7 + [vp]
+    L.gint_batch_destroy.restype = None
+    L.gint_batch_destroy.argtypes = [vp]
     L.gint_sync.restype = i32
     L.gint_sync.argtypes = [vp, vp]
     L.gint_get_info.restype = i32
@@ -129,6 +135,10 @@ class Gint:
         grid = np.ascontiguousarray(grid, dtype=np.int32).reshape(3)
         self.n_atoms = pos.shape[0]
         self.grid = tuple(int(x) for x in grid)
+        self.pos = pos.copy()
+        self.cell = cell.reshape(3, 3).copy()
+        self.omega = float(abs(np.linalg.det(self.cell)))
+        self.dV = self.omega / float(self.grid[0] * self.grid[1] * self.grid[2])
         keep = []
         sps = (_Species * len(species))()
         for s, S in enumerate(species):
