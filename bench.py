@@ -30,6 +30,7 @@ WORKLOADS = {
     # name: (description, tbg index m)
     "tbg_m29": ("twisted bilayer graphene m=29, 10444 C atoms, DZP, rc 7 bohr, h=pi/20 bohr", 29),
     "tbg_m15": ("twisted bilayer graphene m=15, 2884 C atoms, DZP, rc 7 bohr, h=pi/20 bohr", 15),
+    "tbg_m10": ("twisted bilayer graphene m=10, 1324 C atoms, DZP, rc 7 bohr, h=pi/20 bohr", 10),
     "tbg_m5": ("twisted bilayer graphene m=5, 364 C atoms, DZP, rc 7 bohr, h=pi/20 bohr", 5),
 }
 METRIC = "grid pts/s for gint H^V+rho(+force), mixed vs FP64 form at stated error, TBG 10,444"
@@ -373,15 +374,19 @@ def run_ours(args):
             errors["fp64"] = sample_errors(samples, H_fp64, rho_fp64, F_fp64, blocks, offsets)
         errors["sample"] = "oracle outputs at the cpu_baseline sample (random points, blocks, atoms)"
 
-    # vlocal kernel + mirror; rho (+ D format on the tensor path) + empty-brick fill; force (+ D format) + finalize
-    launches_per_step = 6 if prec in ("fp64", "fp32") else 8
+    # vlocal kernel + mirror; rho (+ D format on the tensor path) + empty-brick fill; force (+ D format) + finalize;
+    # the exact form adds a row-maximum pass over D before each D format
+    launches_per_step = {"fp64": 6, "fp32": 6, "fp16x4": 10}.get(prec, 8)
+    gb = lambda n: f"{n * 8 / 1e9:.1f} GB"  # noqa: E731
+    l2_note = (f"inputs larger than L2 (V {gb(ng)}, rho {gb(ng)}, D {gb(g.n_values)})" if ng * 8 > 256e6 else
+               f"V {gb(ng)}, rho {gb(ng)}, D {gb(g.n_values)}: not larger than L2 (profiling / test size)")
     line = {"metric": METRIC, "value": value, "unit": "grid_points/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16x3": "f16x3", "bf16x3": "bf16x3"}.get(prec, prec),
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16x3": "f16x3", "bf16x3": "bf16x3", "fp16x4": "f16x4"}.get(prec, prec),
             "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "grid": list(system.grid),
                        "grid_points": ng, "atoms": system.n_atoms, "precision": prec,
-                       "brick": list(info["brick"]), "l2": "inputs larger than L2 (V 5.1 GB, rho 5.1 GB)",
+                       "brick": list(info["brick"]), "l2": l2_note,
                        "parallelism": "replicas" if ws > 1 else "single"},
             "ms_per_call": {"vlocal": parts[0], "rho": parts[1], "force_stress": parts[2]},
             "fp64_form": fp64, "errors_vs_oracle": errors, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,

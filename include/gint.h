@@ -170,6 +170,12 @@ gint_status gint_force_stress(gint_handle* h, const double* V, const double* D, 
  *   - Calls no cudaMalloc, cudaFree or other allocating routine. */
 gint_status gint_vlocal_static(gint_handle* h, const double* V, double* H, gint_stream stream);
 
+/* Whether the kernels of the handle's current precision accept its bricks
+ * (the tensor-core forms bound the orbitals, atom images and points of one
+ * brick).  GINT_OK, or GINT_ERR_UNSUPPORTED with the limits in
+ * gint_last_error(); host only, launches nothing. */
+gint_status gint_check(const gint_handle* h);
+
 /* Many cells in one launch (the uneven multi-cell workload: many small
  * periodic cells, each with its own handle).  gint_batch_create takes n
  * handles of one device (the handles must outlive the batch).  gint_batch_run

@@ -1,71 +1,114 @@
-"""Many cells in one launch (gint_batch_*) and a brick-shape autotuner.
+"""Many cells in one launch (gint_batch_*) and the brick-shape autotuner.
 
-The autotuner times the three calls of candidate brick shapes on a sample of
-cells (each candidate set up on each sampled cell; shapes the tensor-core
-path cannot take are skipped) and keeps the shape with the least total time,
-in the spirit of the paper's start-up tile autotuning (Section 2.3.3).
+The autotuner times the three calls (H^V, rho, force/stress) for each
+candidate brick shape on a sample of the cells.  It ranks the shapes by total
+time. Each cell of a batch then takes the best-ranked shape that the kernels of
+its precision accept.  The start-up tile tuning of Section 2.3.3 is the model.
 """
 from __future__ import annotations
 
 import ctypes
 import time
-from typing import Sequence
+from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
 
 from . import gint as _g
 
-CANDIDATE_BRICKS = ((8, 8, 8), (8, 8, 4), (4, 8, 8), (4, 4, 8), (4, 4, 4), (3, 3, 4))
+CANDIDATE_BRICKS: Tuple[Tuple[int, int, int], ...] = ((8, 8, 8), (4, 8, 8), (4, 4, 8), (4, 4, 4), (3, 3, 4))
 
 
-def _time_calls(h, V, D, reps=1):
+def _inputs(system, g):
+    import synth
+    V = synth.v_grid(system.grid, synth.plane_wave_params(), device="cuda")
+    blocks, offsets = g.pattern()
+    D = synth.d_fill_torch(blocks, offsets[:-1], g.n_values, system.pos, system.cell, system.nw(), "cuda")
+    return V, D
+
+
+def _time_calls(g, V, D, reps=2):
     import torch
-    h.vlocal(V); h.rho(D); h.force_stress(V, D)
+    g.vlocal(V); g.rho(D); g.force_stress(V, D)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(reps):
-        h.vlocal(V); h.rho(D); h.force_stress(V, D)
+        g.vlocal(V); g.rho(D); g.force_stress(V, D)
     torch.cuda.synchronize()
+    g.sync()
     return (time.perf_counter() - t0) / reps
 
 
-def autotune_brick(systems: Sequence, precision="fp16x3", candidates=CANDIDATE_BRICKS, sample=6, seed=0):
-    """Brick shape with the least vlocal + rho + force time over a sample of the systems.
+def autotune_brick(systems: Sequence, precision="fp16x3", candidates=CANDIDATE_BRICKS, sample=4, seed=0):
+    """Rank candidate brick shapes by the time of vlocal + rho + force on a sample of the systems.
 
-    Returns (brick, {brick: seconds or None}) -- None where the shape is not supported.
+    Returns (ranking, table): ranking lists the shapes from fastest to slowest
+    (shapes that some sampled system cannot take come last, by their time on
+    the systems that take them), table maps shape -> {system index: seconds or None}.
     """
-    import torch
-
-    import synth
     rng = np.random.default_rng(seed)
-    idx = rng.choice(len(systems), size=min(sample, len(systems)), replace=False)
-    times = {}
+    idx = [int(i) for i in rng.choice(len(systems), size=min(sample, len(systems)), replace=False)]
+    table: Dict[tuple, Dict[int, Optional[float]]] = {}
+    inputs = {}
     for brick in candidates:
-        tot = 0.0
-        ok = True
+        brick = tuple(brick)
+        table[brick] = {}
         for i in idx:
-            s = systems[int(i)]
             try:
-                h = _g.from_system(s, precision=precision, brick=brick)
-                V = synth.v_grid(s.grid, synth.plane_wave_params(), device="cuda")
-                bl, off = h.pattern()
-                D = synth.d_fill_torch(bl, off[:-1], h.n_values, s.pos, s.cell, s.nw(), "cuda")
-                tot += _time_calls(h, V, D)
-                h.sync()
-                h.close()
+                g = _g.from_system(systems[i], precision=precision, brick=brick)
             except _g.GintError:
-                ok = False
-                break
-        times[brick] = tot if ok else None
-    best = min((t, b) for b, t in times.items() if t is not None)[1]
-    return best, times
+                table[brick][i] = None  # the brick tables do not fit (setup rejects the shape)
+                continue
+            try:
+                if not g.supported():
+                    table[brick][i] = None
+                    continue
+                V, D = _inputs(systems[i], g)
+                table[brick][i] = _time_calls(g, V, D)
+            finally:
+                g.close()
+    def key(b):
+        t = table[b]
+        missing = sum(v is None for v in t.values())
+        return (missing, sum(v for v in t.values() if v is not None))
+    ranking = sorted(table, key=key)
+    return ranking, table
+
+
+def brick_for(system, precision, ranking) -> Tuple[int, int, int]:
+    """The first shape of the ranking that the kernels of `precision` accept for `system`."""
+    for brick in ranking:
+        try:
+            g = _g.from_system(system, precision=precision, brick=brick)
+        except _g.GintError:
+            continue
+        ok = g.supported()
+        g.close()
+        if ok:
+            return tuple(brick)
+    raise _g.GintError(6, f"no candidate brick shape fits {system.name} in precision {precision}")
 
 
 class GintBatch:
-    """Handles for many cells and one graph launch of all their calls."""
+    """Handles for many cells and one CUDA-graph launch of all their calls.
 
-    def __init__(self, systems: Sequence, precision="fp16x3", brick=(8, 8, 8)):
-        self.handles = [_g.from_system(s, precision=precision, brick=brick) for s in systems]
+    brick: one shape for every cell, a list with one shape per cell, or "auto"
+    (autotune on a sample, then each cell takes the best shape it supports).
+    """
+
+    def __init__(self, systems: Sequence, precision="fp16x3", brick="auto", candidates=CANDIDATE_BRICKS,
+                 sample=4):
+        self.ranking = None
+        if isinstance(brick, str):
+            if brick != "auto":
+                raise ValueError("brick must be a shape, a list of shapes or 'auto'")
+            self.ranking, self.tuning = autotune_brick(systems, precision, candidates, sample)
+            bricks = [brick_for(s, precision, self.ranking) for s in systems]
+        elif len(brick) == 3 and all(isinstance(x, (int, np.integer)) for x in brick):
+            bricks = [tuple(brick)] * len(systems)
+        else:
+            bricks = [tuple(b) for b in brick]
+        self.bricks: List[tuple] = bricks
+        self.handles = [_g.from_system(s, precision=precision, brick=b) for s, b in zip(systems, bricks)]
         L = _g.load()
         arr = (ctypes.c_void_p * len(self.handles))(*[h._h.value for h in self.handles])
         out = ctypes.c_void_p()
@@ -84,13 +127,27 @@ class GintBatch:
             pass
 
     def run(self, V, D, H=None, rho=None, F=None, sigma=None, E=None, stream=None):
-        """Run every cell's calls as one graph launch; arguments are lists of CUDA tensors (or None)."""
+        """All cells' calls as one graph launch; each argument is a list of CUDA float64 tensors (or None)."""
         n = len(self.handles)
 
-        def ptrs(lst):
+        def ptrs(lst, name, numel=None):
             if lst is None:
                 return None
-            return (ctypes.c_void_p * n)(*[None if t is None else t.data_ptr() for t in lst])
+            if len(lst) != n:
+                raise ValueError(f"{name}: need {n} tensors")
+            out = (ctypes.c_void_p * n)()
+            for i, t in enumerate(lst):
+                if t is None:
+                    continue
+                if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
+                    raise TypeError(f"{name}[{i}] must be a contiguous CUDA float64 tensor")
+                if numel is not None and t.numel() < numel(i):
+                    raise ValueError(f"{name}[{i}] holds {t.numel()} values, needs {numel(i)}")
+                out[i] = t.data_ptr()
+            return out
 
-        _g._check(_g.load().gint_batch_run(self._b, ptrs(V), ptrs(D), ptrs(H), ptrs(rho), ptrs(F), ptrs(sigma),
-                                           ptrs(E), _g.Gint._stream(stream)))
+        h = self.handles
+        args = [ptrs(V, "V", lambda i: h[i].n_grid), ptrs(D, "D", lambda i: h[i].n_values),
+                ptrs(H, "H", lambda i: h[i].n_values), ptrs(rho, "rho", lambda i: h[i].n_grid),
+                ptrs(F, "F", lambda i: 3 * h[i].n_atoms), ptrs(sigma, "sigma", lambda _: 9), ptrs(E, "E", lambda _: 1)]
+        _g._check(_g.load().gint_batch_run(self._b, *args, _g.Gint._stream(stream)))

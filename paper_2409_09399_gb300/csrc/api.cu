@@ -12,6 +12,8 @@ gint_status launch_rho_empty(gint_handle* h, double* rho, cudaStream_t st);
 gint_status launch_force_finalize(gint_handle* h, double* F, double* sigma, double* virial, double* E,
                                   cudaStream_t st);
 gint_status tc_vlocal(gint_handle* h, int form, const double* V, double* H, cudaStream_t st);
+gint_status tc_vlocal_check(const gint_handle* h, int form);
+gint_status tc_rhoforce_check(const gint_handle* h);
 gint_status tc_rhoforce(gint_handle* h, int form, bool force, const double* V, const double* D, double* rho,
                         double* facc, double* acc_e, cudaStream_t st);
 
@@ -71,6 +73,17 @@ gint_status gint_vlocal(gint_handle* h, const double* V, double* H, int accumula
         s = simt_run(h, 0, fp32, V, nullptr, H, nullptr, nullptr, st);
     if (s != GINT_OK) return s;
     return launch_mirror(h, H, st);
+}
+
+gint_status gint_check(const gint_handle* h) {
+    set_error("");
+    if (!h) { set_error("gint_check: NULL handle"); return GINT_ERR_INVALID_ARG; }
+    bool fp32 = false;
+    gint_status s = check_precision(h, &fp32);
+    if (s != GINT_OK || !is_tc(h)) return s;
+    s = tc_vlocal_check(h, tc_form(h));
+    if (s != GINT_OK) return s;
+    return tc_rhoforce_check(h);
 }
 
 gint_status gint_rho(gint_handle* h, const double* D, double* rho, gint_stream stream) {

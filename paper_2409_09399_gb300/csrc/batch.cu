@@ -1,19 +1,26 @@
 // batch.cu -- many cells in one launch: the H^V, rho and force/stress calls of
-// every cell of a batch are captured once into a CUDA graph (on an internal
-// stream) and the graph is then launched as one unit on the caller's stream.
-// A later call with different buffers re-captures.
+// every cell of a batch are captured once into a CUDA graph and the graph is
+// then launched as one unit on the caller's stream.  The cells are dealt to
+// kBranches independent branches of the graph (capture forks onto internal
+// streams), so the kernels of small cells overlap.  A later call with
+// different buffers re-captures.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
 #include "gint_impl.cuh"
+
+constexpr int kBranches = 4;
 
 struct gint_batch {
     int n = 0;
     int device = 0;
     std::vector<gint_handle*> h;
     std::vector<const void*> key;  // buffers of the captured graph
-    cudaStream_t cap = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaStream_t cap = nullptr;    // capture origin, also branch 0
+    cudaStream_t br[kBranches] = {};
+    cudaEvent_t ev_join[kBranches] = {};
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -53,15 +60,16 @@ gint_status gint_batch_create(int n, gint_handle* const* handles, gint_batch** o
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    b->br[0] = b->cap;
+    for (int k = 1; k < kBranches && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&b->br[k], cudaStreamNonBlocking);
+    for (int k = 0; k < kBranches && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
     gint_status s = GINT_OK;
     if (e != cudaSuccess) { set_error("gint_batch_create: %s", cudaGetErrorString(e)); s = GINT_ERR_CUDA; }
     for (int i = 0; i < n && s == GINT_OK; ++i) s = tc_prepare(b->h[i]);
     if (prev >= 0) cudaSetDevice(prev);
     if (s != GINT_OK) {
-        if (b->cap) cudaStreamDestroy(b->cap);
-        if (b->ev_in) cudaEventDestroy(b->ev_in);
-        if (b->ev_out) cudaEventDestroy(b->ev_out);
-        delete b;
+        gint_batch_destroy(b);
         return s;
     }
     *out = b;
@@ -74,9 +82,14 @@ void gint_batch_destroy(gint_batch* b) {
     cudaGetDevice(&prev);
     cudaSetDevice(b->device);
     batch_free_graph(b);
+    for (int k = 1; k < kBranches; ++k)
+        if (b->br[k]) cudaStreamDestroy(b->br[k]);
+    for (int k = 0; k < kBranches; ++k)
+        if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (prev >= 0) cudaSetDevice(prev);
     delete b;
 }
@@ -106,16 +119,31 @@ gint_status gint_batch_run(gint_batch* b, const double* const* V, const double* 
     cudaError_t e = cudaSuccess;
     if (!b->exec || key != b->key) {
         batch_free_graph(b);
-        // capture every cell's calls on the internal stream
+        // capture every cell's calls: fork onto the branches, deal the cells round robin, join
         e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
-        if (e != cudaSuccess) { set_error("cudaStreamBeginCapture: %s", cudaGetErrorString(e)); s = GINT_ERR_CUDA; }
+        if (e != cudaSuccess) {
+            set_error("cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+            if (prev >= 0) cudaSetDevice(prev);
+            return GINT_ERR_CUDA;
+        }
+        const int nbr = std::min(kBranches, n);
+        int forked = 1;
+        e = cudaEventRecord(b->ev_fork, b->cap);
+        for (int k = 1; k < nbr && e == cudaSuccess; ++k, ++forked) e = cudaStreamWaitEvent(b->br[k], b->ev_fork, 0);
+        if (e != cudaSuccess) { set_error("gint_batch_run: fork: %s", cudaGetErrorString(e)); s = GINT_ERR_CUDA; }
         for (int i = 0; i < n && s == GINT_OK; ++i) {
-            gint_stream cs = (gint_stream)b->cap;
+            gint_stream cs = (gint_stream)b->br[i % nbr];
             if (H && H[i]) s = gint_vlocal(b->h[i], V[i], H[i], 0, cs);
             if (s == GINT_OK && rho && rho[i]) s = gint_rho(b->h[i], D[i], rho[i], cs);
             if (s == GINT_OK && ((F && F[i]) || (sigma && sigma[i]) || (E && E[i])))
                 s = gint_force_stress(b->h[i], V[i], D[i], F ? F[i] : nullptr, sigma ? sigma[i] : nullptr, nullptr,
                                       E ? E[i] : nullptr, cs);
+        }
+        // join every forked branch (also after an error, so that the capture can end)
+        for (int k = 1; k < forked; ++k) {
+            cudaError_t ej = cudaEventRecord(b->ev_join[k], b->br[k]);
+            if (ej == cudaSuccess) ej = cudaStreamWaitEvent(b->cap, b->ev_join[k], 0);
+            if (ej != cudaSuccess && s == GINT_OK) { set_error("gint_batch_run: join: %s", cudaGetErrorString(ej)); s = GINT_ERR_CUDA; }
         }
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);

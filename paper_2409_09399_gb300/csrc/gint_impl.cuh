@@ -130,6 +130,7 @@ struct gint_handle {
     double* d_facc = nullptr;         // per-atom force and virial accumulators, n_atoms x 12
     double* d_red = nullptr;          // small FP64 reduction buffer ([0] energy)
     void* d_dt = nullptr;             // per-call 16x16 tensor-core copy of D (1 KB per block)
+    int* d_dq = nullptr;              // exact form: per (atom, orbital row) max |D| bits, n_atoms x 16
     void* d_scratch = nullptr;
     size_t scratch_bytes = 0;
     int n_ctas = 0;                   // persistent CTAs of the SIMT kernels

@@ -792,7 +792,7 @@ static void free_handle(gint_handle* h) {
     cudaSetDevice(h->device);
     void* ptrs[] = {h->d_sp, h->d_coef64, h->d_coef32, h->d_ext, h->d_blocks, h->d_offsets, h->d_row_start,
                     h->d_mirror, h->d_brick_start, h->d_brick_atoms, h->d_work, h->d_empty, h->d_err, h->d_red,
-                    h->d_scratch, h->d_nw_atom, h->d_facc, h->d_dt};
+                    h->d_scratch, h->d_nw_atom, h->d_facc, h->d_dt, h->d_dq};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (prev >= 0) cudaSetDevice(prev);

@@ -19,15 +19,15 @@
 // Measured errors of the three-product form grow with the number of MMA
 // additions per element (96 per brick) the way a rounding biased towards zero
 // in the FP32 accumulator predicts, and the bias does not average out over the
-// bricks that add into one H element.  The exact form
-// (fp16x4) avoids that bias for the leading term: every operand value x of row
-// (orbital) o is written as x / q_o = n + l with q_o = 2^qe_o a per-orbital
-// quantum (|x| <= 127 q_o for every point), n = rint(x / q_o) an integer of at
-// most 8 bits and l = x / q_o - n in fp16.  Products n_a n_b are integers below
-// 2^14, so their sums over <= 1024 points stay below 2^24 and accumulate
-// exactly in FP32; the cross terms n l + l n + l l (2^-7 of the leading term)
-// go to a second accumulator.  Each output column then takes two TMEM columns,
-// so a pass holds 256 output columns instead of 512.
+// bricks that add into one H element.  The exact form (fp16x4) avoids that
+// bias for the leading term: every operand value x of row (orbital) o is
+// written as x / q_o = n + l1 + l2 with q_o = 2^qe_o a per-orbital quantum
+// (|x| <= 127 q_o at every point), n = rint(x / q_o) an integer of at most 8
+// bits and l1, l2 two fp16 pieces of the remainder.  Products n_a n_b are
+// integers below 2^14, so their sums over <= 512 points stay below 2^23 and
+// accumulate exactly in FP32; the cross terms n l1 + l1 n + l1 l1 + n l2 + l2 n
+// (2^-7 of the leading term) go to a second accumulator.  Each output column
+// then takes two TMEM columns, so a pass holds 256 output columns.
 // The atom-to-brick displacement is taken in FP64 once per (brick, atom) and
 // split into two FP32 words; in-brick offsets are FP32.
 #include <algorithm>
@@ -44,16 +44,28 @@ constexpr int kTcProdThreads = 512;   // 16 producer warps: two halves, one per 
 constexpr int kTcHalf = kTcProdThreads / 2;
 constexpr int kTcThreads = kTcProdThreads + 32;  // + one MMA-issuing warp
 constexpr int kTcChunk = 16;        // points per K chunk (one MMA K step)
-constexpr int kTcMaxRows = 640;     // padded brick orbitals (5 tiles of 128)
 constexpr int kTcMaxAtoms = 64;     // atom images per brick
-constexpr int kTcMaxPts = 1024;     // points per brick on this path
 constexpr int kTcMaxSpecies = 8;
 constexpr int kTcMaxSeg = 16;       // (row tile, column range) segments per brick
 constexpr long kWaitLimit = 1L << 26;  // bounded mbarrier polls
 
-// bytes of one 16-bit operand piece for one chunk: rows x 16 points x 2 B
-constexpr int kPieceBytes = kTcMaxRows * kTcChunk * 2;
-constexpr int kBufBytes = 4 * kPieceBytes;  // A_hi, A_lo, B_hi, B_lo
+// Sizes of the two forms (up to 640 padded orbital rows, 5 tiles of 128, in both).
+// Three-product form: pieces A_hi, A_lo, B_hi, B_lo over all rows; up to 1024
+// points per brick.  Exact form: pieces A_n, A_l1, A_l2 for the row tiles of
+// the current pass only (a pass of <= 256 output columns spans at most three
+// row tiles) and B_n, B_l1, B_l2 over all rows; up to 512 points per brick
+// (the integer products of 512 points stay below 2^23).
+template <bool kExact> struct TcCfg {
+    static constexpr int kPieces = kExact ? 3 : 2;            // pieces per operand
+    static constexpr int kRows = 640;
+    static constexpr int kARows = kExact ? 384 : 640;         // rows held by an A piece
+    static constexpr int kPts = kExact ? 512 : 1024;
+    static constexpr int kAPieceBytes = kARows * kTcChunk * 2;  // rows x 16 points x 2 B
+    static constexpr int kBPieceBytes = kRows * kTcChunk * 2;
+    static constexpr int kBOff = kPieces * kAPieceBytes;        // first B piece in a buffer
+    static constexpr int kBufBytes = kPieces * (kAPieceBytes + kBPieceBytes);
+    static constexpr int kPassCols = kExact ? 256 : 512;      // output columns per pass
+};
 
 struct TcAtom {
     float c_hi[3], c_lo[3];  // (brick origin - atom image position), FP64 split into two FP32 words
@@ -69,20 +81,22 @@ struct TcArgs {
     int* counter;
 };
 
-struct TcSmem {
-    unsigned char buf[2][kBufBytes];
+template <bool kExact> struct TcSmem {
+    using C = TcCfg<kExact>;
+    unsigned char buf[2][C::kBufBytes];
     TcAtom at[kTcMaxAtoms];
-    int64_t pairoff[kTcMaxAtoms * kTcMaxAtoms];
-    float4 pt[kTcMaxPts];           // in-brick offset of each point (x, y, z) and 2^s V dV
+    int pairblk[kTcMaxAtoms * (kTcMaxAtoms + 1) / 2];  // block of image pair a1 <= a2 (index a2 (a2+1)/2 + a1), -1 if none
+    float4 pt[C::kPts];             // in-brick offset of each point (x, y, z) and 2^s V dV
     SpeciesFast spf[kTcMaxSpecies];
-    unsigned char row_atom[kTcMaxRows];
-    unsigned char row_mu[kTcMaxRows];
-    unsigned short rowtab[kTcMaxRows];  // byte offset of row r's 16-byte segment in a piece
-    float row_q[kTcMaxRows];            // exact form: quantum 2^qe of row r
+    unsigned char row_atom[C::kRows];
+    unsigned char row_mu[C::kRows];
+    unsigned short rowtab[C::kRows];  // byte offset of row r's 16-byte segment in a piece
+    float row_q[C::kRows];            // exact form: quantum 2^qe of row r
     unsigned char seg_tile[kTcMaxSeg];  // segment: row tile, columns [c0, c1), TMEM column
     short seg_c0[kTcMaxSeg], seg_c1[kTcMaxSeg], seg_tcol[kTcMaxSeg];
     int pass_first[kTcMaxSeg + 1];      // first segment of each pass
     int npass, nrow, ncol;
+    float wmax[kTcThreads / 32];
     uint64_t full[2];   // producers of buffer b arrived (kTcHalf arrivals)
     uint64_t empty[2];  // MMAs reading buffer b completed (tcgen05.commit)
     uint64_t done;      // all MMAs of the pass completed
@@ -92,7 +106,9 @@ struct TcSmem {
     float scale_inv;
 };
 
-static_assert(sizeof(TcSmem) + 1024 <= 232448, "shared memory of the H^V kernel exceeds 227 KB");
+static_assert(sizeof(TcSmem<false>) + 1024 <= 232448, "shared memory of the H^V kernel exceeds 227 KB");
+static_assert(sizeof(TcSmem<true>) + 1024 <= 232448, "shared memory of the exact H^V kernel exceeds 227 KB");
+__host__ __device__ constexpr int pair_index(int a1, int a2) { return a2 * (a2 + 1) / 2 + a1; }  // a1 <= a2
 
 // Offset (bytes) of element (row r, point q) of one piece: core matrix
 // (r / 8, q / 8) at ((r / 8) * 2 + q / 8) * 128, inside it row r % 8 of 16 bytes.
@@ -120,22 +136,28 @@ template <> struct Conv<__nv_bfloat16> {
     static constexpr int bf16 = 1;
 };
 
-// Exact form: s = n + l with n = rint(s) (|s| <= 127.5, so n is exact in fp16) and l = s - n in fp16.
-__device__ __forceinline__ void fix_split(float s, unsigned short& hi, unsigned short& lo) {
+// Exact form: s = n + l1 + l2 with n = rint(s) (|s| <= 128, so n is exact in
+// fp16), l1 = fp16(s - n), l2 = fp16(s - n - l1) (both differences exact in FP32).
+__device__ __forceinline__ void fix_split3(float s, unsigned short& n16, unsigned short& l1, unsigned short& l2) {
     const float n = rintf(s);
-    hi = __half_as_ushort(__float2half_rn(n));
-    lo = __half_as_ushort(__float2half_rn(s - n));
+    const float r = s - n;
+    const __half h1 = __float2half_rn(r);
+    n16 = __half_as_ushort(__float2half_rn(n));
+    l1 = __half_as_ushort(h1);
+    l2 = __half_as_ushort(__float2half_rn(r - __half2float(h1)));
 }
 __device__ __forceinline__ float exp2i(int e) { return __int_as_float((127 + e) << 23); }  // 2^e, |e| < 127
 
 template <typename H16, bool kExact>
 __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const double* V, double* H) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
+    TcSmem<kExact>& S = *reinterpret_cast<TcSmem<kExact>*>(smem_raw);
+    using C = TcCfg<kExact>;
+    constexpr int kPassCols = C::kPassCols;
+    constexpr int kAP = C::kAPieceBytes, kBP = C::kBPieceBytes, kBOff = C::kBOff;
     const Problem& P = A.P;
     const GridDev& g = P.g;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr int kPassCols = kExact ? 256 : 512;  // output columns per pass
 
     if (warp == 0) {
         tc::tmem_alloc(&S.tmem, 512);
@@ -151,7 +173,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
         S.abort = 0;
     }
     if (tid < P.n_species) species_fast_from(P.sp[tid], S.spf[tid]);
-    for (int r = tid; r < kTcMaxRows; r += kTcThreads) S.rowtab[r] = (unsigned short)((((r >> 3) * (kTcChunk / 8)) << 7) + ((r & 7) << 4));
+    for (int r = tid; r < C::kRows; r += kTcThreads) S.rowtab[r] = (unsigned short)((((r >> 3) * (kTcChunk / 8)) << 7) + ((r & 7) << 4));
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -208,12 +230,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
             wmax = fmaxf(wmax, fabsf(wv));
         }
         for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-        __shared__ float s_wmax[kTcThreads / 32];
-        if (lane == 0) s_wmax[warp] = wmax;
+        if (lane == 0) S.wmax[warp] = wmax;
         __syncthreads();
         if (tid == 0) {
             float m = 0.f;
-            for (int k = 0; k < kTcThreads / 32; ++k) m = fmaxf(m, s_wmax[k]);
+            for (int k = 0; k < kTcThreads / 32; ++k) m = fmaxf(m, S.wmax[k]);
             int e = 0;
             if (m > 0.f) frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
             S.scale_inv = ldexpf(1.f, e);
@@ -261,7 +282,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
         for (int q = tid; q < na * na; q += kTcThreads) {
             const int a1 = q / na, a2 = q - a1 * na;
             if (a1 > a2) continue;
-            int64_t off = -1;
+            int off = -1;
             const TcAtom &X = S.at[a1], &Y = S.at[a2];
             // FP32 distance with a margin: only pairs within rc1 + rc2 are looked up
             const float dx = (Y.c_hi[0] - X.c_hi[0]) + (Y.c_lo[0] - X.c_lo[0]);
@@ -271,19 +292,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
             const float cut = P.sp[X.sp].rc_f + P.sp[Y.sp].rc_f;
             if (dist < cut + 1e-3f) {
                 const int64_t blk = find_block(P, X.I, Y.I, Y.t[0] - X.t[0], Y.t[1] - X.t[1], Y.t[2] - X.t[2]);
-                if (blk >= 0) off = P.offsets[blk];
+                if (blk >= 0) off = (int)blk;
                 else if (dist < cut - 1e-3f) atomicOr(P.err, kErrPatternMissing);
             }
-            S.pairoff[a1 * na + a2] = off;
+            S.pairblk[pair_index(a1, a2)] = off;
         }
-        // zero the padding rows [nrow, round128(nrow)) of both chunk buffers
+        // zero the padding rows [nrow, round128(nrow)) of both chunk buffers (B pieces; A pieces
+        // too in the three-product form, where A holds every row)
         const int nrow128 = (nrow + 127) & ~127;
         for (int b = 0; b < 2; ++b)
             for (int e = tid; e < (nrow128 - nrow) * kTcChunk; e += kTcThreads) {
                 const int r = nrow + e / kTcChunk, q = e % kTcChunk;
                 const int o = piece_off(r, q);
-                for (int pc = 0; pc < 4; ++pc)
-                    *reinterpret_cast<unsigned short*>(&S.buf[b][pc * kPieceBytes + o]) = 0;
+                for (int pc = 0; pc < C::kPieces; ++pc) {
+                    *reinterpret_cast<unsigned short*>(&S.buf[b][kBOff + pc * kBP + o]) = 0;
+                    if (!kExact) *reinterpret_cast<unsigned short*>(&S.buf[b][pc * kAP + o]) = 0;
+                }
             }
         __syncthreads();
 
@@ -291,6 +315,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
         for (int pass = 0; pass < npass && !S.abort; ++pass) {
             const int s0p = S.pass_first[pass], s1p = S.pass_first[pass + 1];
             const int row_lo = 128 * S.seg_tile[s0p];  // rows below this are not read in this pass
+            // exact form: A pieces hold rows [a_lo, a_hi) of this pass's row tiles (<= 384 rows)
+            const int a_lo = kExact ? row_lo : 0;
+            const int a_hi = kExact ? 128 * (S.seg_tile[s1p - 1] + 1) : C::kRows;
+            if (kExact) {
+                // zero A rows [max(nrow, a_lo), a_hi) (they may hold rows of the previous pass;
+                // every MMA of that pass has completed)
+                const int z0 = max(nrow, a_lo);
+                for (int b = 0; b < 2; ++b)
+                    for (int e = tid; e < (a_hi - z0) * kTcChunk; e += kTcThreads) {
+                        const int r = z0 - a_lo + e / kTcChunk, q = e % kTcChunk;
+                        const int o = piece_off(r, q);
+                        for (int pc = 0; pc < C::kPieces; ++pc) *reinterpret_cast<unsigned short*>(&S.buf[b][pc * kAP + o]) = 0;
+                    }
+                __syncthreads();
+            }
             if (!issuer_warp) {
                 // ---- producers: half h fills buffer h with chunks c = h, h + 2, ...
                 const int b = half;
@@ -299,9 +338,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
                     if (uses[b] > 0 && !S.abort && !tc::mbar_wait(&S.empty[b], (uses[b] - 1) & 1, kWaitLimit))
                         atomicOr(&S.abort, 1);
                     // orbital values at the chunk's points, two points per item, for atom
-                    // images with rows this pass reads
-                    for (int item = lt; item < na * (kTcChunk / 2); item += kTcHalf) {
-                        const int a = item / (kTcChunk / 2), qp = item - a * (kTcChunk / 2);
+                    // images with rows this pass reads.  Item bits: [1:0] point pair within a
+                    // half chunk, [4:2] atom within a group of 8, [5] half chunk, [6..] atom
+                    // group; so a warp stores 8 atoms (distinct rows mod 8) x 4 point pairs of
+                    // the same 16-byte row segment half: 32 different banks.
+                    const int n_items = ((na + 7) >> 3) << 6;
+                    for (int item = lt; item < n_items; item += kTcHalf) {
+                        const int a = ((item >> 6) << 3) | ((item >> 2) & 7);
+                        const int qp = (((item >> 5) & 1) << 2) | (item & 3);
+                        if (a >= na) continue;
                         const TcAtom& X = S.at[a];
                         if (X.off + X.nw <= row_lo) continue;
                         const int q = 2 * qp;
@@ -318,31 +363,49 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
                         const int rbase = X.off;
                         const SpeciesFast& sf = S.spf[X.sp];
                         auto put2 = [&](int o, float va, float vb) {
-                            unsigned short ah0, al0, bh0, bl0, ah1, al1, bh1, bl1;
+                            const int r = rbase + o;
+                            const int offB = kBOff + S.rowtab[r] + qoff;
+                            auto stB = [&](int pc, unsigned short x0, unsigned short x1) {
+                                *reinterpret_cast<uint32_t*>(&buf[offB + pc * kBP]) = x0 | ((uint32_t)x1 << 16);
+                            };
                             if (kExact) {
                                 const float qi = exp2i(-sf.qe[o]);
                                 va *= qi;
                                 vb *= qi;
-                                fix_split(va * wa, ah0, al0);
-                                fix_split(vb * wb, ah1, al1);
-                                fix_split(va, bh0, bl0);
-                                fix_split(vb, bh1, bl1);
+                                unsigned short n0, p0, r0, n1, p1, r1;
+                                if (r >= a_lo && r < a_hi) {
+                                    const int offA = S.rowtab[r - a_lo] + qoff;
+                                    fix_split3(va * wa, n0, p0, r0);
+                                    fix_split3(vb * wb, n1, p1, r1);
+                                    *reinterpret_cast<uint32_t*>(&buf[offA]) = n0 | ((uint32_t)n1 << 16);
+                                    *reinterpret_cast<uint32_t*>(&buf[offA + kAP]) = p0 | ((uint32_t)p1 << 16);
+                                    *reinterpret_cast<uint32_t*>(&buf[offA + 2 * kAP]) = r0 | ((uint32_t)r1 << 16);
+                                }
+                                fix_split3(va, n0, p0, r0);
+                                fix_split3(vb, n1, p1, r1);
+                                stB(0, n0, n1); stB(1, p0, p1); stB(2, r0, r1);
                             } else {
+                                unsigned short ah0, al0, bh0, bl0, ah1, al1, bh1, bl1;
                                 Conv<H16>::split(va * wa, ah0, al0);
                                 Conv<H16>::split(vb * wb, ah1, al1);
                                 Conv<H16>::split(va, bh0, bl0);
                                 Conv<H16>::split(vb, bh1, bl1);
+                                const int offA = S.rowtab[r] + qoff;
+                                *reinterpret_cast<uint32_t*>(&buf[offA]) = ah0 | ((uint32_t)ah1 << 16);
+                                *reinterpret_cast<uint32_t*>(&buf[offA + kAP]) = al0 | ((uint32_t)al1 << 16);
+                                stB(0, bh0, bh1); stB(1, bl0, bl1);
                             }
-                            const int off = S.rowtab[rbase + o] + qoff;
-                            *reinterpret_cast<uint32_t*>(&buf[0 * kPieceBytes + off]) = ah0 | ((uint32_t)ah1 << 16);
-                            *reinterpret_cast<uint32_t*>(&buf[1 * kPieceBytes + off]) = al0 | ((uint32_t)al1 << 16);
-                            *reinterpret_cast<uint32_t*>(&buf[2 * kPieceBytes + off]) = bh0 | ((uint32_t)bh1 << 16);
-                            *reinterpret_cast<uint32_t*>(&buf[3 * kPieceBytes + off]) = bl0 | ((uint32_t)bl1 << 16);
                         };
                         if (!orbitals_fast2(sf, coef4, ax, ay, az, bx, by, bz, put2))
                             for (int o = 0; o < X.nw; ++o) {
-                                const int off = S.rowtab[rbase + o] + qoff;
-                                for (int pc = 0; pc < 4; ++pc) *reinterpret_cast<uint32_t*>(&buf[pc * kPieceBytes + off]) = 0u;
+                                const int r = rbase + o;
+                                const int offB = kBOff + S.rowtab[r] + qoff;
+                                const bool inA = r >= a_lo && r < a_hi;
+                                const int offA = inA ? S.rowtab[r - a_lo] + qoff : 0;
+                                for (int pc = 0; pc < C::kPieces; ++pc) {
+                                    *reinterpret_cast<uint32_t*>(&buf[offB + pc * kBP]) = 0u;
+                                    if (inA) *reinterpret_cast<uint32_t*>(&buf[offA + pc * kAP]) = 0u;
+                                }
                             }
                     }
                     tc::fence_async_smem();
@@ -363,24 +426,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
                     if (!S.abort) {
                         for (int sg = s0p; sg < s1p; ++sg) {
                             const int i = S.seg_tile[sg], c_end = S.seg_c1[sg];
-                            const uint32_t a_hi = base + 0 * kPieceBytes + (uint32_t)(i * 16) * sbo;
-                            const uint32_t a_lo = base + 1 * kPieceBytes + (uint32_t)(i * 16) * sbo;
+                            const uint32_t arow = (uint32_t)((128 * i - a_lo) >> 3) * sbo;  // tile i in the A pieces
+                            const uint32_t pa0 = base + arow;
+                            const uint32_t pa1 = base + kAP + arow;
+                            const uint32_t pa2 = base + 2 * kAP + arow;  // exact form
                             for (int c0 = S.seg_c0[sg]; c0 < c_end; c0 += 256) {
                                 const int nn = min(256, c_end - c0);
                                 const uint32_t idesc = tc::idesc_f16(128, nn, Conv<H16>::bf16, 0, 0);
-                                const uint32_t b_hi = base + 2 * kPieceBytes + (uint32_t)(c0 >> 3) * sbo;
-                                const uint32_t b_lo = base + 3 * kPieceBytes + (uint32_t)(c0 >> 3) * sbo;
+                                const uint32_t pb0 = base + kBOff + (uint32_t)(c0 >> 3) * sbo;
+                                const uint32_t pb1 = pb0 + kBP;
+                                const uint32_t pb2 = pb0 + 2 * kBP;  // exact form
                                 const uint32_t d = tmem + (uint32_t)(S.seg_tcol[sg] + c0 - S.seg_c0[sg]);
-                                tc::mma_f16(d, tc::smem_desc(a_hi, lbo, sbo), tc::smem_desc(b_hi, lbo, sbo), idesc, c > 0 ? 1u : 0u);
+                                tc::mma_f16(d, tc::smem_desc(pa0, lbo, sbo), tc::smem_desc(pb0, lbo, sbo), idesc, c > 0 ? 1u : 0u);
                                 if (kExact) {
                                     // integer products alone in d; the cross terms in d + 256
                                     const uint32_t d1 = d + 256;
-                                    tc::mma_f16(d1, tc::smem_desc(a_hi, lbo, sbo), tc::smem_desc(b_lo, lbo, sbo), idesc, c > 0 ? 1u : 0u);
-                                    tc::mma_f16(d1, tc::smem_desc(a_lo, lbo, sbo), tc::smem_desc(b_hi, lbo, sbo), idesc, 1u);
-                                    tc::mma_f16(d1, tc::smem_desc(a_lo, lbo, sbo), tc::smem_desc(b_lo, lbo, sbo), idesc, 1u);
+                                    tc::mma_f16(d1, tc::smem_desc(pa0, lbo, sbo), tc::smem_desc(pb1, lbo, sbo), idesc, c > 0 ? 1u : 0u);
+                                    tc::mma_f16(d1, tc::smem_desc(pa1, lbo, sbo), tc::smem_desc(pb0, lbo, sbo), idesc, 1u);
+                                    tc::mma_f16(d1, tc::smem_desc(pa1, lbo, sbo), tc::smem_desc(pb1, lbo, sbo), idesc, 1u);
+                                    tc::mma_f16(d1, tc::smem_desc(pa0, lbo, sbo), tc::smem_desc(pb2, lbo, sbo), idesc, 1u);
+                                    tc::mma_f16(d1, tc::smem_desc(pa2, lbo, sbo), tc::smem_desc(pb0, lbo, sbo), idesc, 1u);
                                 } else {
-                                    tc::mma_f16(d, tc::smem_desc(a_hi, lbo, sbo), tc::smem_desc(b_lo, lbo, sbo), idesc, 1u);
-                                    tc::mma_f16(d, tc::smem_desc(a_lo, lbo, sbo), tc::smem_desc(b_hi, lbo, sbo), idesc, 1u);
+                                    tc::mma_f16(d, tc::smem_desc(pa0, lbo, sbo), tc::smem_desc(pb1, lbo, sbo), idesc, 1u);
+                                    tc::mma_f16(d, tc::smem_desc(pa1, lbo, sbo), tc::smem_desc(pb0, lbo, sbo), idesc, 1u);
                                 }
                             }
                         }
@@ -425,8 +493,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
                             if (col >= nrow) continue;
                             const int a2 = S.row_atom[col];
                             if (a1 > a2) continue;
-                            const int64_t off = S.pairoff[a1 * na + a2];
-                            if (off < 0) continue;
+                            const int blk = S.pairblk[pair_index(a1, a2)];
+                            if (blk < 0) continue;
+                            const int64_t off = __ldg(P.offsets + blk);
                             const int nu = S.row_mu[col];
                             // scale factors are powers of two: exact
                             const double val = kExact ? ((double)v[jj] + (double)v1[jj]) * (double)(qr * S.row_q[col])
@@ -460,23 +529,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
+template <bool kExact> size_t tc_smem_bytes() { return sizeof(TcSmem<kExact>) + 1024; }
 
 // form: 0 = fp16x3, 1 = bf16x3, 2 = fp16x4 (exact leading term)
-gint_status tc_vlocal(gint_handle* h, int form, const double* V, double* H, cudaStream_t st) {
-    if (h->n_work == 0) return GINT_OK;
-    if (h->max_brick_orb > kTcMaxRows || h->max_brick_atoms > kTcMaxAtoms || h->grid.bpad > kTcMaxPts ||
+gint_status tc_vlocal_check(const gint_handle* h, int form) {
+    const bool exact = form == 2;
+    const int max_rows = exact ? TcCfg<true>::kRows : TcCfg<false>::kRows;
+    const int max_pts = exact ? TcCfg<true>::kPts : TcCfg<false>::kPts;
+    if (h->max_brick_orb > max_rows || h->max_brick_atoms > kTcMaxAtoms || h->grid.bpad > max_pts ||
         h->grid.bpad % kTcChunk != 0 || h->n_species > kTcMaxSpecies) {
         set_error("tensor-core form needs <= %d orbitals, <= %d atom images and <= %d points per brick and "
-                  "<= %d species (have %d, %d, %d, %d); use smaller bricks", kTcMaxRows, kTcMaxAtoms, kTcMaxPts,
+                  "<= %d species (have %d, %d, %d, %d); use smaller bricks", max_rows, kTcMaxAtoms, max_pts,
                   kTcMaxSpecies, h->max_brick_orb, h->max_brick_atoms, h->grid.bpad, h->n_species);
         return GINT_ERR_UNSUPPORTED;
     }
+    return GINT_OK;
+}
+
+gint_status tc_vlocal(gint_handle* h, int form, const double* V, double* H, cudaStream_t st) {
+    gint_status s = tc_vlocal_check(h, form);
+    if (s != GINT_OK || h->n_work == 0) return s;
+    const bool exact = form == 2;
     TcArgs A;
     A.P = h->problem();
     A.counter = h->d_err + 2;
     GINT_CUDA_TRY(cudaMemsetAsync(A.counter, 0, sizeof(int), st));
-    const size_t smem = tc_smem_bytes();
+    const size_t smem = exact ? tc_smem_bytes<true>() : tc_smem_bytes<false>();
 #define GINT_LAUNCH_VL(H16, X)                                                                                 \
     do {                                                                                                       \
         GINT_CUDA_TRY(cudaFuncSetAttribute(k_vlocal_tc<H16, X>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \

@@ -16,6 +16,13 @@
 //     K-major core-matrix order), so a B row is two 16-byte copies per piece;
 //   * G accumulates in TMEM (lane = point), three products per step
 //     (hi*hi + hi*lo + lo*hi);
+//   * exact form (fp16x4): both operands in fixed point, x / q = n + l1 + l2
+//     with n an integer of at most 8 bits and l1, l2 fp16 pieces of the
+//     remainder; q is one power of two for all orbital values (the largest
+//     per-orbital bound) and, for D, one per (atom, orbital row) taken from the
+//     largest |D| of that row this call.  Products n*n accumulate exactly in
+//     TMEM columns [0, 256) (K <= 1024, products below 2^14); the cross terms
+//     n l1 + l1 n + l1 l1 + n l2 + l2 n go to columns [256, 512);
 //   * the epilogue thread of point p reads G_p, re-evaluates the orbital
 //     values (and gradients for the force) of every active image at p and
 //     forms rho_p = sum phi G, or F_I += 2 W_p grad phi . G with the virial
@@ -34,9 +41,23 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxAtoms = 64;
 constexpr int kMaxCols = 512;            // TMEM columns (packed orbitals of one M-tile)
-constexpr int kBRowsMax = 512;
-constexpr int kAPiece = 128 * 16 * 2;    // 128 points x 16 orbitals x 2 B
-constexpr int kBPiece = kBRowsMax * 16 * 2;
+// A pieces (128 points x 16 orbital slots) are MN-major: core matrix (point group
+// pg = p / 8, orbital group og = o / 8) holds 8 orbital rows of 8 points (16 B);
+// point groups are kASbo = 144 B apart (128 B + 16 B of padding, so that the 32
+// points of a warp storing one orbital hit 16 different banks), orbital groups
+// kALbo = 16 * 144 B apart.
+constexpr int kASbo = 144;
+constexpr int kALbo = 16 * kASbo;
+constexpr int kAPiece = 2 * kALbo;
+constexpr int kDtPiece = 512;            // one 16 x 16 piece of a pre-formatted D block
+constexpr int kDtBytes = 3 * kDtPiece;   // per block: up to three pieces (exact form)
+
+// Per form: pieces per operand and B rows (= output columns of a column group).
+template <bool kExact> struct RfCfg {
+    static constexpr int kPieces = kExact ? 3 : 2;
+    static constexpr int kBRows = kExact ? 256 : 512;
+    static constexpr int kBPiece = kBRows * 16 * 2;
+};
 constexpr long kWait = 1L << 26;
 constexpr int kMaxSpecies = 8;
 
@@ -46,9 +67,10 @@ struct Atom {
     int t[3];
 };
 
-struct Smem {
-    unsigned char A[2][2][2 * kAPiece];   // [buffer][image of the step][hi | lo]
-    unsigned char B[2][2][2 * kBPiece];
+template <bool kExact> struct Smem {
+    using C = RfCfg<kExact>;
+    unsigned char A[2][2][C::kPieces * kAPiece];   // [buffer][image of the step][pieces]
+    unsigned char B[2][2][C::kPieces * C::kBPiece];
     Atom at[kMaxAtoms];
     int pairblk[kMaxAtoms * kMaxAtoms];  // block (I_a2, I_a1, T_a1 - T_a2) for K image a1, N image a2; -1 if none
     float W2[kMaxBrickPts];              // 2 V dV (force)
@@ -65,7 +87,18 @@ struct Smem {
     int work, abort, nact, ncols;
 };
 
-static_assert(sizeof(Smem) + 1024 <= 232448, "shared memory of the rho/force kernel exceeds 227 KB");
+static_assert(sizeof(Smem<false>) + 1024 <= 232448, "shared memory of the rho/force kernel exceeds 227 KB");
+static_assert(sizeof(Smem<true>) + 1024 <= 232448, "shared memory of the exact rho/force kernel exceeds 227 KB");
+
+// Exact form: s = n + l1 + l2 (n = rint(s), |s| <= 128; l1, l2 fp16 pieces of s - n).
+__device__ __forceinline__ void fix_split3(float s, unsigned short& n16, unsigned short& l1, unsigned short& l2) {
+    const float n = rintf(s);
+    const float r = s - n;
+    const __half h1 = __float2half_rn(r);
+    n16 = __half_as_ushort(__float2half_rn(n));
+    l1 = __half_as_ushort(h1);
+    l2 = __half_as_ushort(__float2half_rn(r - __half2float(h1)));
+}
 
 template <typename H16> struct Split;
 template <> struct Split<__half> {
@@ -88,6 +121,29 @@ template <> struct Split<__nv_bfloat16> {
 // byte offset of element (row r, k) in a K-major piece with 16 K-columns:
 // core (r/8, k/8) at ((r/8)*2 + k/8)*128, row r%8 at *16, column k%8 at *2
 __device__ __forceinline__ int kmaj16(int r, int k) { return ((((r >> 3) << 1) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1); }
+// byte offset of A element (point p, orbital slot o) in an MN-major A piece
+__device__ __forceinline__ int amn(int p, int o) { return (o >> 3) * kALbo + (p >> 3) * kASbo + ((o & 7) << 4) + ((p & 7) << 1); }
+
+// Sum 16 values over the 32 lanes of a warp with 16 shuffles (each step
+// exchanges half of the remaining values with the partner lane).  Afterwards
+// lanes L and L ^ 1 hold the total of value index
+// 8 b4 + 4 b3 + 2 b2 + b1, b_k = bit k of L; the return value is that total.
+__device__ __forceinline__ float warp_sum16(float (&v)[16], int lane) {
+#pragma unroll
+    for (int o = 16, c = 16; o >= 2; o >>= 1, c >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < c / 2; ++k) {
+            const float keep = up ? v[k + c / 2] : v[k];
+            const float send = up ? v[k] : v[k + c / 2];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+__device__ __forceinline__ int warp_sum16_index(int lane) {
+    return (((lane >> 4) & 1) << 3) | (((lane >> 3) & 1) << 2) | (((lane >> 2) & 1) << 1) | ((lane >> 1) & 1);
+}
 
 __device__ __forceinline__ void point_offset(const GridDev& g, int p, float& fx, float& fy, float& fz) {
     const int l2 = p % g.B[2], l1 = (p / g.B[2]) % g.B[1], l0 = p / (g.B[2] * g.B[1]);
@@ -100,9 +156,41 @@ __device__ __forceinline__ void point_offset(const GridDev& g, int p, float& fx,
 // Pre-format D: every block b as a 16 x 16 tile (zero padded) of hi and lo
 // 16-bit pieces in K-major core-matrix order, values of block b taken from its
 // canonical block (transposed when b is not canonical).  One warp per block.
-template <typename H16>
+// Largest |D| of every (atom I, orbital row i) over the blocks (I, J, T), as
+// FP32 bits (non-negative floats order like their bit patterns).
+__global__ void k_dmax(Problem P, const int32_t* mirror, const int* nw_atom, int64_t n_blocks, const double* D,
+                       int* dq) {
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= n_blocks) return;
+    const int32_t* k = P.blocks + 5 * b;
+    const int I = k[0], J = k[1];
+    const bool canon = (I < J) || (I == J && (k[2] > 0 || (k[2] == 0 && (k[3] > 0 || (k[3] == 0 && k[4] >= 0)))));
+    const int64_t src = canon ? b : (int64_t)mirror[b];
+    if (src < 0) return;
+    const int nI = nw_atom[I], nJ = nw_atom[J];
+    const double* Ds = D + P.offsets[src];
+    for (int e = lane; e < 256; e += 32) {
+        const int i = e >> 4, j = e & 15;
+        if (i < nI && j < nJ) {
+            const float v = fabsf((float)(canon ? Ds[i * nJ + j] : Ds[j * nI + i]));
+            if (v > 0.f) atomicMax(dq + 16 * I + i, __float_as_int(v));
+        }
+    }
+}
+
+// 2^e with |D row max| / 127 < 2^e (1 for an all-zero row)
+__device__ __forceinline__ int dq_exp(int bits) {
+    int e = 0;
+    const float m = __int_as_float(bits);
+    if (m > 0.f) frexpf(m * (1.f / 127.f), &e);
+    return max(-100, min(100, e));
+}
+__device__ __forceinline__ float exp2f_i(int e) { return __int_as_float((127 + e) << 23); }  // |e| < 127
+
+template <typename H16, bool kExact>
 __global__ void k_format_d(Problem P, const int32_t* mirror, const int* nw_atom, int64_t n_blocks, const double* D,
-                           unsigned char* Dt) {
+                           const int* dq, unsigned char* Dt) {
     const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (b >= n_blocks) return;
@@ -112,25 +200,30 @@ __global__ void k_format_d(Problem P, const int32_t* mirror, const int* nw_atom,
     const int64_t src = canon ? b : (int64_t)mirror[b];
     const int nI = nw_atom[I], nJ = nw_atom[J];
     const double* Ds = D + P.offsets[src < 0 ? b : src];
-    unsigned char* out = Dt + b * 1024;
+    unsigned char* out = Dt + b * kDtBytes;
     for (int e = lane; e < 256; e += 32) {
         const int i = e >> 4, j = e & 15;
         float v = 0.f;
         if (i < nI && j < nJ && src >= 0) v = (float)(canon ? Ds[i * nJ + j] : Ds[j * nI + i]);
-        unsigned short hi, lo;
-        Split<H16>::run(v, hi, lo);
+        unsigned short hi, lo, l2 = 0;
+        if (kExact) fix_split3(v * exp2f_i(-dq_exp(dq[16 * I + i])), hi, lo, l2);
+        else Split<H16>::run(v, hi, lo);
         const int o = kmaj16(i, j);
         *reinterpret_cast<unsigned short*>(out + o) = hi;
-        *reinterpret_cast<unsigned short*>(out + 512 + o) = lo;
+        *reinterpret_cast<unsigned short*>(out + kDtPiece + o) = lo;
+        if (kExact) *reinterpret_cast<unsigned short*>(out + 2 * kDtPiece + o) = l2;
     }
 }
 
-template <typename H16, bool kForce>
+template <typename H16, bool kForce, bool kExact>
 __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* counter, const double* V,
-                                                            const unsigned char* Dt, double* rho, double* facc,
-                                                            double* acc_e) {
+                                                            const unsigned char* Dt, const int* dq, double* rho,
+                                                            double* facc, double* acc_e) {
+    constexpr int kCols = kExact ? kMaxCols / 2 : kMaxCols;  // output columns of one column group
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    Smem& S = *reinterpret_cast<Smem*>(smem_raw);
+    Smem<kExact>& S = *reinterpret_cast<Smem<kExact>*>(smem_raw);
+    using C = RfCfg<kExact>;
+    constexpr int kBPiece = C::kBPiece;
     const GridDev& g = P.g;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -149,6 +242,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = S.tmem;
+    // exact form: one quantum 2^qa for every orbital value (the largest per-orbital quantum)
+    int qa = -126;
+    if (kExact)
+        for (int sp = 0; sp < P.n_species; ++sp)
+            for (int o = 0; o < S.spf[sp].nw; ++o) qa = max(qa, (int)S.spf[sp].qe[o]);
+    const float qa_inv = kExact ? exp2f_i(-qa) : 1.f, qa_f = kExact ? exp2f_i(qa) : 1.f;
     uint32_t commits[2] = {0, 0};
     uint32_t chunk = 0;  // global chunk counter (buffer parity)
     const float4* coef4 = reinterpret_cast<const float4*>(P.coef32);
@@ -256,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
             // column groups: consecutive active images whose orbitals fit the 512 TMEM columns
             for (int cg0 = 0; cg0 < nact && !S.abort;) {
             int cg1 = cg0;
-            while (cg1 < nact && S.rowoff[cg1 + 1] - S.rowoff[cg0] <= kMaxCols) ++cg1;
+            while (cg1 < nact && S.rowoff[cg1 + 1] - S.rowoff[cg0] <= kCols) ++cg1;
             if (cg1 == cg0) cg1 = cg0 + 1;  // never taken (an image has <= 16 orbitals); keeps the loop finite
             const int rbase = S.rowoff[cg0];
             const int nrows = S.rowoff[cg1] - rbase;
@@ -266,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
                 const int r = nrows + (e >> 1), half = e & 1;
                 for (int b = 0; b < 2; ++b)
                     for (int j = 0; j < 2; ++j)
-                        for (int pc = 0; pc < 2; ++pc)
+                        for (int pc = 0; pc < C::kPieces; ++pc)
                             *reinterpret_cast<uint4*>(&S.B[b][j][pc * kBPiece + kmaj16(r, half * 8)]) = make_uint4(0, 0, 0, 0);
             }
             // ---- K loop over active images, two images (K = 32) per step
@@ -277,9 +376,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
                     if (lane == 0) atomicOr(&S.abort, 1);
                 // B rows (asynchronous copies first): for image a1 = act[k + j] and every active
                 // image a2 of the group, rows nu of block (I_a2, I_a1, T_a1 - T_a2)
-                for (int e = tid; e < nk * nrows * 4; e += kThreads) {
-                    const int j = e / (nrows * 4), rem = e - j * nrows * 4;
-                    const int r = rem >> 2, part = rem & 3;  // part: (piece, half)
+                constexpr int kParts = 2 * C::kPieces;  // (piece, half) per B row
+                for (int e = tid; e < nk * nrows * kParts; e += kThreads) {
+                    const int j = e / (nrows * kParts), rem = e - j * nrows * kParts;
+                    const int r = rem / kParts, part = rem - r * kParts;
                     int lo_j = cg0, hi_j = cg1 - 1;
                     while (lo_j < hi_j) {
                         const int mid = (lo_j + hi_j + 1) >> 1;
@@ -290,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
                     const int blk = S.pairblk[S.act[k + j] * na + a2];
                     const int pc = part >> 1, half = part & 1;
                     unsigned char* dst = &S.B[b][j][pc * kBPiece + kmaj16(r, half * 8)];
-                    if (blk >= 0) tc::cp_async16(dst, Dt + (int64_t)blk * 1024 + pc * 512 + kmaj16(nu, half * 8));
+                    if (blk >= 0) tc::cp_async16(dst, Dt + (int64_t)blk * kDtBytes + pc * kDtPiece + kmaj16(nu, half * 8));
                     else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
                 }
                 // A rows: orbital values of image act[k + j] at point p (16 slots, zero padded)
@@ -300,10 +400,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
                         const Atom& X = S.at[S.act[k + j]];
                         const int p = mt * 128 + pl;
                         unsigned char* A0 = S.A[b][j];
-                        for (int o = X.nw; o < 16; ++o) {
-                            *reinterpret_cast<unsigned short*>(A0 + kmaj16(pl, o)) = 0;
-                            *reinterpret_cast<unsigned short*>(A0 + kAPiece + kmaj16(pl, o)) = 0;
-                        }
+                        for (int o = X.nw; o < 16; ++o)
+                            for (int pc = 0; pc < C::kPieces; ++pc)
+                                *reinterpret_cast<unsigned short*>(A0 + pc * kAPiece + amn(pl, o)) = 0;
                         bool inside = false;
                         if (p < g.bpts) {
                             float fx, fy, fz;
@@ -312,18 +411,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
                             const float dy = (X.c_hi[1] + fy) + X.c_lo[1];
                             const float dz = (X.c_hi[2] + fz) + X.c_lo[2];
                             auto put = [&](int o, float v, float, float, float) {
-                                unsigned short hi, lo;
-                                Split<H16>::run(v, hi, lo);
-                                *reinterpret_cast<unsigned short*>(A0 + kmaj16(pl, o)) = hi;
-                                *reinterpret_cast<unsigned short*>(A0 + kAPiece + kmaj16(pl, o)) = lo;
+                                unsigned short hi, lo, l2 = 0;
+                                if (kExact) fix_split3(v * qa_inv, hi, lo, l2);
+                                else Split<H16>::run(v, hi, lo);
+                                *reinterpret_cast<unsigned short*>(A0 + amn(pl, o)) = hi;
+                                *reinterpret_cast<unsigned short*>(A0 + kAPiece + amn(pl, o)) = lo;
+                                if (kExact) *reinterpret_cast<unsigned short*>(A0 + 2 * kAPiece + amn(pl, o)) = l2;
                             };
                             inside = orbitals_fast<false>(S.spf[X.sp], coef4, dx, dy, dz, put);
                         }
                         if (!inside)
-                            for (int o = 0; o < X.nw; ++o) {
-                                *reinterpret_cast<unsigned short*>(A0 + kmaj16(pl, o)) = 0;
-                                *reinterpret_cast<unsigned short*>(A0 + kAPiece + kmaj16(pl, o)) = 0;
-                            }
+                            for (int o = 0; o < X.nw; ++o)
+                                for (int pc = 0; pc < C::kPieces; ++pc)
+                                    *reinterpret_cast<unsigned short*>(A0 + pc * kAPiece + amn(pl, o)) = 0;
                     }
                 }
                 tc::cp_async_wait_all();
@@ -333,18 +433,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
                 if (tid == 0) {
                     tc::fence_after_sync();
                     for (int j = 0; j < nk; ++j) {
-                        const uint32_t a_hi = tc::smem_u32(S.A[b][j]), a_lo = a_hi + kAPiece;
+                        const uint32_t a_hi = tc::smem_u32(S.A[b][j]), a_lo = a_hi + kAPiece, a_l2 = a_lo + kAPiece;
                         const uint32_t bb = tc::smem_u32(S.B[b][j]);
                         for (int n0 = 0; n0 < ncols; n0 += 256) {
                             const int nn = min(256, ncols - n0);
-                            const uint32_t idesc = tc::idesc_f16(128, nn, Split<H16>::bf16, 0, 0);
-                            const uint32_t b_hi = bb + (n0 >> 3) * 256, b_lo = b_hi + kBPiece;
+                            const uint32_t idesc = tc::idesc_f16(128, nn, Split<H16>::bf16, 1, 0);  // A MN-major
+                            const uint32_t b_hi = bb + (n0 >> 3) * 256, b_lo = b_hi + kBPiece, b_l2 = b_lo + kBPiece;
                             const uint32_t d = tmem + (uint32_t)n0;
-                            // K-major, 16 K-columns: LBO (K-adjacent cores) 128 B, SBO (row groups) 256 B
-                            tc::mma_f16(d, tc::smem_desc(a_hi, 128, 256), tc::smem_desc(b_hi, 128, 256), idesc,
-                                        (k + j) > 0 ? 1u : 0u);
-                            tc::mma_f16(d, tc::smem_desc(a_hi, 128, 256), tc::smem_desc(b_lo, 128, 256), idesc, 1u);
-                            tc::mma_f16(d, tc::smem_desc(a_lo, 128, 256), tc::smem_desc(b_hi, 128, 256), idesc, 1u);
+                            // B K-major with 16 K-columns: LBO (K-adjacent cores) 128 B, SBO (row groups) 256 B;
+                            // A MN-major: LBO (orbital groups) kALbo, SBO (point groups) kASbo
+                            const uint32_t acc = (k + j) > 0 ? 1u : 0u;
+                            tc::mma_f16(d, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_hi, 128, 256), idesc, acc);
+                            if (kExact) {
+                                const uint32_t d1 = d + kCols;  // cross terms
+                                tc::mma_f16(d1, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_lo, 128, 256), idesc, acc);
+                                tc::mma_f16(d1, tc::smem_desc(a_lo, kALbo, kASbo), tc::smem_desc(b_hi, 128, 256), idesc, 1u);
+                                tc::mma_f16(d1, tc::smem_desc(a_lo, kALbo, kASbo), tc::smem_desc(b_lo, 128, 256), idesc, 1u);
+                                tc::mma_f16(d1, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_l2, 128, 256), idesc, 1u);
+                                tc::mma_f16(d1, tc::smem_desc(a_l2, kALbo, kASbo), tc::smem_desc(b_hi, 128, 256), idesc, 1u);
+                            } else {
+                                tc::mma_f16(d, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_lo, 128, 256), idesc, 1u);
+                                tc::mma_f16(d, tc::smem_desc(a_lo, kALbo, kASbo), tc::smem_desc(b_hi, 128, 256), idesc, 1u);
+                            }
                         }
                     }
                     tc::mma_commit(&S.bar[b]);
@@ -376,12 +486,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
                     const Atom& Y = S.at[a2];
                     int c0 = S.rowoff[j] - rbase;
                     int sh = 0;
-                    if (c0 + 16 > kMaxCols) { sh = c0 + 16 - kMaxCols; c0 -= sh; }
+                    if (c0 + 16 > kCols) { sh = c0 + 16 - kCols; c0 -= sh; }
                     float Gv[16];
-                    tc::tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, Gv);
+                    const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
+                    tc::tmem_ld16(ta, Gv);
                     float* gs = S.Gst[warp][lane];
+                    if (kExact) {
+                        // G = (exact integer part + cross terms) x 2^qa x 2^qD(atom, row)
+                        float G1[16];
+                        tc::tmem_ld16(ta + kCols, G1);
+                        const int* dqa = dq + 16 * Y.I;
 #pragma unroll
-                    for (int o = 0; o < 16; ++o) gs[o] = Gv[o];
+                        for (int o = 0; o < 16; ++o) {
+                            const int orow = o - sh;  // orbital of column c0 + o within image a2
+                            const float qd = (orow >= 0 && orow < Y.nw) ? exp2f_i(dq_exp(__ldg(dqa + orow))) : 0.f;
+                            gs[o] = (Gv[o] + G1[o]) * (qa_f * qd);
+                        }
+                    } else {
+#pragma unroll
+                        for (int o = 0; o < 16; ++o) gs[o] = Gv[o];
+                    }
                     const float dx = (Y.c_hi[0] + fx) + Y.c_lo[0];
                     const float dy = (Y.c_hi[1] + fy) + Y.c_lo[1];
                     const float dz = (Y.c_hi[2] + fz) + Y.c_lo[2];
@@ -399,16 +523,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
                         // per point in FP32, summed over the warp's 32 points in FP32,
                         // then accumulated per image in FP64
                         const float w2 = pv ? S.W2[p] : 0.f;
-                        float v[13];
+                        float v[16];
                         v[0] = w2 * f0; v[1] = w2 * f1; v[2] = w2 * f2;
                         const float d3[3] = {dx, dy, dz};
+#pragma unroll
                         for (int a = 0; a < 3; ++a)
+#pragma unroll
                             for (int c = 0; c < 3; ++c) v[3 + 3 * a + c] = v[a] * d3[c];
                         v[12] = 0.5f * w2 * e_j;
-                        for (int o = 16; o > 0; o >>= 1)
-                            for (int q = 0; q < 13; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
-                        if (lane == 0)
-                            for (int q = 0; q < 13; ++q) atomicAdd(&S.red[j][q], (double)v[q]);
+                        v[13] = v[14] = v[15] = 0.f;
+                        const float tot = warp_sum16(v, lane);
+                        const int q = warp_sum16_index(lane);
+                        if (!(lane & 1) && q < 13) atomicAdd(&S.red[j][q], (double)tot);
                     }
                 }
                 if (warp >= 4) S.rho_half[pl] = rho_p;
@@ -447,9 +573,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
 
 // ------------------------------------------------------------------ host
 static gint_status ensure_dt(gint_handle* h) {
-    if (h->d_dt) return GINT_OK;
-    const size_t bytes = (size_t)std::max<int64_t>(1, h->n_blocks) * 1024;
-    GINT_CUDA_TRY(cudaMalloc(&h->d_dt, bytes));
+    if (!h->d_dt) {
+        const size_t bytes = (size_t)std::max<int64_t>(1, h->n_blocks) * kDtBytes;
+        GINT_CUDA_TRY(cudaMalloc(&h->d_dt, bytes));
+    }
+    if (!h->d_dq) GINT_CUDA_TRY(cudaMalloc(&h->d_dq, sizeof(int) * 16 * (size_t)std::max(1, h->n_atoms)));
     return GINT_OK;
 }
 
@@ -463,38 +591,56 @@ gint_status tc_prepare(gint_handle* h) {
     return s;
 }
 
-gint_status tc_rhoforce(gint_handle* h, int bf16, bool force, const double* V, const double* D, double* rho,
-                        double* facc, double* acc_e, cudaStream_t st) {
+// form: 0 = fp16x3, 1 = bf16x3, 2 = fp16x4 (exact leading term)
+gint_status tc_rhoforce_check(const gint_handle* h) {
     if (h->max_brick_atoms > kMaxAtoms || h->max_nw > 16 || h->n_species > kMaxSpecies) {
         set_error("tensor-core rho/force needs <= %d atom images per brick, <= 16 orbitals per atom and <= %d "
                   "species (have %d, %d, %d); use smaller bricks", kMaxAtoms, kMaxSpecies, h->max_brick_atoms,
                   h->max_nw, h->n_species);
         return GINT_ERR_UNSUPPORTED;
     }
-    gint_status s = ensure_dt(h);
+    return GINT_OK;
+}
+
+gint_status tc_rhoforce(gint_handle* h, int form, bool force, const double* V, const double* D, double* rho,
+                        double* facc, double* acc_e, cudaStream_t st) {
+    gint_status s = tc_rhoforce_check(h);
+    if (s != GINT_OK) return s;
+    s = ensure_dt(h);
     if (s != GINT_OK) return s;
     Problem P = h->problem();
+    const bool exact = form == 2;
     if (h->n_blocks > 0) {
-        const int64_t threads = h->n_blocks * 32;
-        if (bf16) k_format_d<__nv_bfloat16><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(P, h->d_mirror, h->d_nw_atom, h->n_blocks, D, (unsigned char*)h->d_dt);
-        else k_format_d<__half><<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(P, h->d_mirror, h->d_nw_atom, h->n_blocks, D, (unsigned char*)h->d_dt);
+        const unsigned grid = (unsigned)((h->n_blocks * 32 + 255) / 256);
+        unsigned char* dt = (unsigned char*)h->d_dt;
+        if (exact) {
+            GINT_CUDA_TRY(cudaMemsetAsync(h->d_dq, 0, sizeof(int) * 16 * (size_t)h->n_atoms, st));
+            k_dmax<<<grid, 256, 0, st>>>(P, h->d_mirror, h->d_nw_atom, h->n_blocks, D, h->d_dq);
+            k_format_d<__half, true><<<grid, 256, 0, st>>>(P, h->d_mirror, h->d_nw_atom, h->n_blocks, D, h->d_dq, dt);
+        } else if (form == 1) {
+            k_format_d<__nv_bfloat16, false><<<grid, 256, 0, st>>>(P, h->d_mirror, h->d_nw_atom, h->n_blocks, D, h->d_dq, dt);
+        } else {
+            k_format_d<__half, false><<<grid, 256, 0, st>>>(P, h->d_mirror, h->d_nw_atom, h->n_blocks, D, h->d_dq, dt);
+        }
         GINT_CUDA_TRY(cudaGetLastError());
     }
     if (h->n_work == 0) return GINT_OK;
     int* counter = h->d_err + 2;
     GINT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
-    const size_t smem = sizeof(Smem) + 1024;
+    const size_t smem = (exact ? sizeof(Smem<true>) : sizeof(Smem<false>)) + 1024;
     const unsigned char* Dt = (const unsigned char*)h->d_dt;
-#define GINT_LAUNCH_RF(H16, F)                                                                                  \
+#define GINT_LAUNCH_RF(H16, F, X)                                                                              \
     do {                                                                                                        \
-        GINT_CUDA_TRY(cudaFuncSetAttribute(k_rhoforce_tc<H16, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+        GINT_CUDA_TRY(cudaFuncSetAttribute(k_rhoforce_tc<H16, F, X>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                            (int)smem));                                                         \
-        k_rhoforce_tc<H16, F><<<h->sm_count, kThreads, smem, st>>>(P, counter, V, Dt, rho, facc, acc_e);        \
+        k_rhoforce_tc<H16, F, X><<<h->sm_count, kThreads, smem, st>>>(P, counter, V, Dt, h->d_dq, rho, facc, acc_e); \
     } while (0)
-    if (bf16) {
-        if (force) GINT_LAUNCH_RF(__nv_bfloat16, true); else GINT_LAUNCH_RF(__nv_bfloat16, false);
+    if (form == 1) {
+        if (force) GINT_LAUNCH_RF(__nv_bfloat16, true, false); else GINT_LAUNCH_RF(__nv_bfloat16, false, false);
+    } else if (exact) {
+        if (force) GINT_LAUNCH_RF(__half, true, true); else GINT_LAUNCH_RF(__half, false, true);
     } else {
-        if (force) GINT_LAUNCH_RF(__half, true); else GINT_LAUNCH_RF(__half, false);
+        if (force) GINT_LAUNCH_RF(__half, true, false); else GINT_LAUNCH_RF(__half, false, false);
     }
 #undef GINT_LAUNCH_RF
     GINT_CUDA_TRY(cudaGetLastError());

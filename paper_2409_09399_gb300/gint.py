@@ -22,7 +22,7 @@ STATUS = {0: "GINT_OK", 1: "GINT_ERR_INVALID_ARG", 2: "GINT_ERR_CUDA", 3: "GINT_
 
 # exported symbols, in the order include/gint.h declares them
 SYMBOLS = ["gint_setup", "gint_destroy", "gint_pattern", "gint_set_precision", "gint_vlocal", "gint_rho",
-           "gint_force_stress", "gint_vlocal_static", "gint_batch_create", "gint_batch_run",
+           "gint_force_stress", "gint_vlocal_static", "gint_check", "gint_batch_create", "gint_batch_run",
            "gint_batch_destroy", "gint_sync", "gint_get_info", "gint_work_stats", "gint_last_error"]
 
 
@@ -84,6 +84,8 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.gint_force_stress.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     L.gint_vlocal_static.restype = i32
     L.gint_vlocal_static.argtypes = [vp, vp, vp, vp]
+    L.gint_check.restype = i32
+    L.gint_check.argtypes = [vp]
     L.gint_batch_create.restype = i32
     L.gint_batch_create.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp)]
     L.gint_batch_run.restype = i32
@@ -135,6 +137,7 @@ class Gint:
         grid = np.ascontiguousarray(grid, dtype=np.int32).reshape(3)
         self.n_atoms = pos.shape[0]
         self.grid = tuple(int(x) for x in grid)
+        self.n_grid = self.grid[0] * self.grid[1] * self.grid[2]
         self.pos = pos.copy()
         self.cell = cell.reshape(3, 3).copy()
         self.omega = float(abs(np.linalg.det(self.cell)))
@@ -186,6 +189,15 @@ class Gint:
     def set_precision(self, precision):
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         _check(load().gint_set_precision(self._h, p))
+
+    def supported(self) -> bool:
+        """Whether the kernels of the current precision accept this handle's bricks."""
+        st = load().gint_check(self._h)
+        if st == 0:
+            return True
+        if st == 6:  # GINT_ERR_UNSUPPORTED
+            return False
+        _check(st)
 
     def info(self) -> dict:
         inf = _Info()

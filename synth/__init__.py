@@ -34,10 +34,11 @@ _M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
 
 def splitmix64(x: np.ndarray) -> np.ndarray:
     """SplitMix64 finaliser applied elementwise to uint64 ``x`` (wraps mod 2^64)."""
-    z = np.asarray(x, dtype=np.uint64) + np.uint64(0x9E3779B97F4A7C15)
-    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
-    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
-    return z ^ (z >> np.uint64(31))
+    with np.errstate(over="ignore"):
+        z = np.asarray(x, dtype=np.uint64) + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
 
 
 def hash_keys(seed: int, *keys) -> np.ndarray:

@@ -1,0 +1,106 @@
+"""Batched launch over many uneven cells (gint_batch_*): one CUDA graph holding
+every cell's H^V, rho and force/stress calls, brick shapes from the autotuner,
+per-cell error of the mixed form against the FP64 form, and the FP64 batch
+against the oracle on the smallest cells."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+N_CELLS = 12
+
+
+def _cells():
+    return [synth.random_cell(i) for i in range(N_CELLS)]
+
+
+def _run_batch(b, systems, Vs, Ds):
+    import torch
+    H = [torch.empty(h.n_values, dtype=torch.float64, device="cuda") for h in b.handles]
+    rho = [torch.empty(h.grid, dtype=torch.float64, device="cuda") for h in b.handles]
+    F = [torch.empty((h.n_atoms, 3), dtype=torch.float64, device="cuda") for h in b.handles]
+    sig = [torch.empty((3, 3), dtype=torch.float64, device="cuda") for h in b.handles]
+    E = [torch.empty(1, dtype=torch.float64, device="cuda") for h in b.handles]
+    b.run(Vs, Ds, H, rho, F, sig, E)
+    torch.cuda.synchronize()
+    for h in b.handles:
+        h.sync()
+    return H, rho, F, sig, E
+
+
+def test_batch_mixed_vs_single_and_fp64(cuda):
+    import torch
+    from paper_2409_09399_gb300 import gint
+    from paper_2409_09399_gb300.batch import GintBatch
+    systems = _cells()
+    b = GintBatch(systems, precision="fp16x3", brick="auto", candidates=((8, 8, 8), (4, 4, 8), (4, 4, 4)), sample=3)
+    print("autotuner ranking", b.ranking, "bricks", b.bricks)
+    Vs, Ds = [], []
+    for s, h in zip(systems, b.handles):
+        blocks, offsets = h.pattern()
+        Vs.append(synth.v_grid(s.grid, synth.plane_wave_params(), device="cuda"))
+        Ds.append(synth.d_fill_torch(blocks, offsets[:-1], h.n_values, s.pos, s.cell, s.nw(), "cuda"))
+    H, rho, F, sig, E = _run_batch(b, systems, Vs, Ds)
+    # a second launch with new output buffers re-captures; with the same ones it replays
+    H2, rho2, F2, sig2, E2 = _run_batch(b, systems, Vs, Ds)
+    worst = {"H": 0.0, "rho": 0.0, "F": 0.0}
+    for i, (s, h) in enumerate(zip(systems, b.handles)):
+        # same kernels one cell at a time: equal up to the order of FP64 atomics
+        Hs = h.vlocal(Vs[i])
+        rs = h.rho(Ds[i])
+        Fs, ss, _, Es = h.force_stress(Vs[i], Ds[i])
+        h.sync()
+        for got in (H[i], H2[i]):
+            assert torch.allclose(got, Hs, rtol=0, atol=1e-12 * float(Hs.abs().max()))
+        for got in (rho[i], rho2[i]):
+            assert torch.allclose(got, rs, rtol=0, atol=1e-12 * float(rs.abs().max()))
+        assert torch.allclose(F[i], Fs, rtol=0, atol=1e-12 * max(1.0, float(Fs.abs().max())))
+        assert torch.allclose(sig[i], ss, rtol=0, atol=1e-12)
+        assert abs(float(E[i]) - float(Es)) <= 1e-12 * abs(float(Es))
+        # per-cell error against the FP64 form
+        g64 = gint.from_system(s, precision="fp64", brick=b.bricks[i])
+        H64 = g64.vlocal(Vs[i])
+        r64 = g64.rho(Ds[i])
+        F64, s64, _, E64 = g64.force_stress(Vs[i], Ds[i])
+        g64.sync()
+        eH = float((H[i] - H64).abs().max())
+        eR = float((rho[i] - r64).abs().max() / r64.abs().max())
+        eF = float((F[i] - F64).abs().max())
+        print(f"cell {i}: {s.n_atoms} atoms grid {s.grid[0]} brick {b.bricks[i]}: H {eH:.2e} rho {eR:.2e} F {eF:.2e}")
+        worst["H"] = max(worst["H"], eH)
+        worst["rho"] = max(worst["rho"], eR)
+        worst["F"] = max(worst["F"], eF)
+        g64.close()
+    print("worst per-cell error vs FP64:", worst)
+    assert worst["H"] < 5e-5 and worst["rho"] < 1e-4 and worst["F"] < 1e-4
+
+
+def test_batch_fp64_vs_oracle(cuda):
+    """FP64 cells through the batch graph against the oracle (the two smallest grids)."""
+    import torch
+    from paper_2409_09399_gb300.batch import GintBatch
+    systems = _cells()
+    order = np.argsort([np.prod(s.grid) for s in systems])[:2]
+    sel = [systems[i] for i in order]
+    b = GintBatch(sel, precision="fp64", brick=(4, 4, 4))
+    Vs = [synth.v_grid(s.grid, synth.plane_wave_params(), device="cuda") for s in sel]
+    Ds = []
+    for s, h in zip(sel, b.handles):
+        blocks, offsets = h.pattern()
+        Ds.append(synth.d_fill_torch(blocks, offsets[:-1], h.n_values, s.pos, s.cell, s.nw(), "cuda"))
+    H, rho, F, sig, E = _run_batch(b, sel, Vs, Ds)
+    for i, s in enumerate(sel):
+        o = oracle.Oracle(s)
+        Vn = Vs[i].cpu().numpy()
+        Dn = o.d_fill()
+        H_ref = o.vlocal(Vn)
+        r_ref = o.rho(Dn)
+        F_ref, W_ref = o.force(Vn, Dn)
+        eH = np.max(np.abs(H[i].cpu().numpy() - H_ref)) / np.max(np.abs(H_ref))
+        eR = np.max(np.abs(rho[i].cpu().numpy() - r_ref)) / np.max(np.abs(r_ref))
+        eF = np.max(np.abs(F[i].cpu().numpy() - F_ref)) / max(1.0, np.max(np.abs(F_ref)))
+        print(f"fp64 cell {s.name}: H {eH:.2e} rho {eR:.2e} F {eF:.2e}")
+        assert eH < 1e-11 and eR < 1e-11 and eF < 1e-10

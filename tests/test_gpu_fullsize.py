@@ -15,6 +15,7 @@ pytestmark = pytest.mark.gpu
 TOL = {
     "fp64": {"H": 1e-11, "rho": 1e-11, "F": 1e-10},
     "fp16x3": {"H": 5e-5, "rho": 5e-5, "F": 5e-5},
+    "fp16x4": {"H": 1e-7, "rho": 1e-6, "F": 1e-5},
 }
 
 
@@ -57,7 +58,7 @@ def run_case(m, precision, n_blocks=12, n_points=400, n_atoms=2, seed=0):
     return eH, eR, eF, eE
 
 
-@pytest.mark.parametrize("m,precision", [(29, "fp16x3"), (5, "fp64"), (15, "fp16x3")])
+@pytest.mark.parametrize("m,precision", [(29, "fp16x3"), (29, "fp16x4"), (5, "fp64"), (15, "fp16x3")])
 def test_fullsize_sampled(m, precision, cuda):
     eH, eR, eF, eE = run_case(m, precision)
     tol = TOL[precision]

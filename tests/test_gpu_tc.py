@@ -9,6 +9,16 @@ pytestmark = pytest.mark.gpu
 
 _cache = {}
 
+# Stated accuracy of each form: max abs for H and F, normwise for rho.  The
+# three-product forms carry the bias of the tensor-core FP32 accumulation; the
+# exact form (fp16x4) meets the target accuracy H <= 1e-7 Ha, rho <= 1e-6
+# (normwise), F <= 1e-5 Ha/bohr.
+TOL = {
+    "fp16x3": {"H": 5e-5, "rho": 1e-4, "F": 1e-4, "sigma": 1e-4},
+    "bf16x3": {"H": 5e-5, "rho": 1e-4, "F": 1e-4, "sigma": 1e-4},
+    "fp16x4": {"H": 1e-7, "rho": 1e-6, "F": 1e-5, "sigma": 1e-6},
+}
+
 
 def diamond_case():
     if "diamond" not in _cache:
@@ -19,7 +29,7 @@ def diamond_case():
     return _cache["diamond"]
 
 
-@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3"])
+@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3", "fp16x4"])
 @pytest.mark.parametrize("brick", [(3, 3, 4), (4, 3, 3)])
 def test_tc_vlocal_diamond_full(precision, brick, cuda):
     import torch
@@ -32,10 +42,10 @@ def test_tc_vlocal_diamond_full(precision, brick, cuda):
     print(f"{precision} brick {brick}: max |H - H_ref| = {err:.3e} (max |H_ref| {np.abs(H_ref).max():.3f})")
     # split 16-bit operands with FP32 accumulation in tensor memory: the error is
     # set by the accumulator (~2^-23 |partial| per accumulation step)
-    assert err < 5e-5
+    assert err < TOL[precision]["H"]
 
 
-@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3"])
+@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3", "fp16x4"])
 def test_tc_vlocal_tbg_sampled(precision, cuda):
     import torch
     from paper_2409_09399_gb300 import gint
@@ -56,10 +66,10 @@ def test_tc_vlocal_tbg_sampled(precision, cuda):
         got = H[offsets[b]:offsets[b + 1]].reshape(ref[k].shape)
         err = max(err, np.max(np.abs(got - ref[k])))
     print(f"{precision} TBG m=2: max |H - H_ref| over {len(sel)} blocks = {err:.3e}")
-    assert err < 5e-5
+    assert err < TOL[precision]["H"]
 
 
-@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3"])
+@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3", "fp16x4"])
 def test_tc_rho_force_diamond(precision, cuda):
     """rho and force/stress on the tensor cores against the oracle (diamond, 3x3x4 bricks)."""
     import torch
@@ -83,12 +93,13 @@ def test_tc_rho_force_diamond(precision, cuda):
     sig_ref = -W_ref.sum(0) / o.omega
     e_sig = np.max(np.abs(sigma.cpu().numpy() - sig_ref))
     print(f"{precision}: rho normwise {e_rho:.3e}  F abs {e_F:.3e} (max {np.abs(F_ref).max():.3f})  sigma abs {e_sig:.3e}")
-    assert e_rho < 1e-4
-    assert e_F < 1e-4
-    assert e_sig < 1e-4
+    tol = TOL[precision]
+    assert e_rho < tol["rho"]
+    assert e_F < tol["F"]
+    assert e_sig < tol["sigma"]
 
 
-@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3"])
+@pytest.mark.parametrize("precision", ["fp16x3", "bf16x3", "fp16x4"])
 def test_tc_rho_force_tbg_sampled(precision, cuda):
     import torch
     from paper_2409_09399_gb300 import gint
@@ -114,5 +125,5 @@ def test_tc_rho_force_tbg_sampled(precision, cuda):
     F_ref, _ = o.force(V, D_or, atoms=atoms)
     e_F = np.max(np.abs(F.cpu().numpy()[atoms] - F_ref))
     print(f"{precision} TBG m=2: rho normwise {e_rho:.3e}  F abs {e_F:.3e} (max {np.abs(F_ref).max():.3f})")
-    assert e_rho < 1e-4
-    assert e_F < 1e-4
+    assert e_rho < TOL[precision]["rho"]
+    assert e_F < TOL[precision]["F"]
