@@ -101,7 +101,17 @@ def dist_env():
 
 
 # ----------------------------------------------------------------- oracle arm
-def oracle_sample(system, n_points, n_blocks, n_atoms_f, seed=11):
+def oracle_inputs(system):
+    """The oracle and its inputs for `system` (input generation and set-up, never timed)."""
+    import oracle
+    import synth
+    o = oracle.Oracle(system)
+    V = synth.v_grid(system.grid, synth.plane_wave_params()).numpy()
+    D = o.d_fill()
+    return o, V, D
+
+
+def oracle_sample(system, n_points, n_blocks, n_atoms_f, seed=11, inputs=None):
     """Time the FP64 oracle on a bounded random sample and scale to the whole step.
 
     Returns (seconds for one full step as extrapolated, description, sampled
@@ -110,14 +120,8 @@ def oracle_sample(system, n_points, n_blocks, n_atoms_f, seed=11):
     atoms.  Each part is scaled by (total / sampled).
     """
     import numpy as np
-
-    import oracle
-    import synth
     rng = np.random.default_rng(seed)
-    o = oracle.Oracle(system)
-    params = synth.plane_wave_params()
-    V = synth.v_grid(system.grid, params).numpy()  # input generation, not timed
-    D = o.d_fill()
+    o, V, D = inputs if inputs is not None else oracle_inputs(system)
     idx = np.stack([rng.integers(0, system.grid[i], n_points) for i in range(3)], 1)
     t0 = time.perf_counter()
     rho_s = o.rho_points(D, idx)
@@ -169,8 +173,10 @@ def run_reference(args):
     cores = oracle.num_threads()
     step_times = []
     sample = None
+    inputs = oracle_inputs(system)
     for i in range(args.warmup + args.steps):
-        t_full, sample, _ = oracle_sample(system, args.ref_points, args.ref_blocks, args.ref_atoms, seed=100 + i)
+        t_full, sample, _ = oracle_sample(system, args.ref_points, args.ref_blocks, args.ref_atoms, seed=100 + i,
+                                          inputs=inputs)
         if i >= args.warmup:
             step_times.append(t_full)
     t = sum(step_times) / len(step_times)
@@ -178,8 +184,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "grid_points/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": name, "description": desc, "grid_points": system.n_grid,
-                       "atoms": system.n_atoms},
+            "config": {"workload": name, "description": desc, "grid": list(system.grid),
+                       "grid_points": system.n_grid, "atoms": system.n_atoms,
+                       "precision": "fp64 (the oracle, plain C + OpenMP on the host cores)"},
             "cpu_baseline": {"value": value, "unit": "grid_points/s", "cores": cores, "kind": "oracle",
                              "sample": json.dumps(sample)},
             "e2e": {"value": value, "unit": "grid_points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -405,7 +412,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tbg_m29")
-    ap.add_argument("--precision", default="fp16x3")
+    ap.add_argument("--precision", default="fp16x4")
     ap.add_argument("--brick", type=int, nargs=3, default=[0, 0, 0])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)

@@ -11,7 +11,7 @@ gint_status launch_mirror(gint_handle* h, double* H, cudaStream_t st);
 gint_status launch_rho_empty(gint_handle* h, double* rho, cudaStream_t st);
 gint_status launch_force_finalize(gint_handle* h, double* F, double* sigma, double* virial, double* E,
                                   cudaStream_t st);
-gint_status tc_vlocal(gint_handle* h, int form, const double* V, double* H, cudaStream_t st);
+gint_status tc_vlocal(gint_handle* h, int form, const double* V, double* H, int accumulate, cudaStream_t st);
 gint_status tc_vlocal_check(const gint_handle* h, int form);
 gint_status tc_rhoforce_check(const gint_handle* h);
 gint_status tc_rhoforce(gint_handle* h, int form, bool force, const double* V, const double* D, double* rho,
@@ -68,7 +68,7 @@ gint_status gint_vlocal(gint_handle* h, const double* V, double* H, int accumula
     cudaStream_t st = (cudaStream_t)stream;
     if (!accumulate && h->n_values > 0) GINT_CUDA_TRY(cudaMemsetAsync(H, 0, sizeof(double) * h->n_values, st));
     if (is_tc(h))
-        s = tc_vlocal(h, tc_form(h), V, H, st);
+        s = tc_vlocal(h, tc_form(h), V, H, accumulate, st);
     else
         s = simt_run(h, 0, fp32, V, nullptr, H, nullptr, nullptr, st);
     if (s != GINT_OK) return s;

@@ -24,6 +24,7 @@ struct SpeciesFast {
     int rad_l[kMaxRadial];
     int orb_base[kMaxRadial];  // first orbital of each radial function
     signed char qe[kMaxNw];    // fixed-point quantum exponent of each orbital (|phi| <= 127 * 2^qe)
+    signed char qeu[kMaxNw];   // the same for the unnormalised orbital phi / ylm_norm
 };
 
 __device__ __forceinline__ void species_fast_from(const SpeciesDev& s, SpeciesFast& f) {
@@ -35,7 +36,10 @@ __device__ __forceinline__ void species_fast_from(const SpeciesDev& s, SpeciesFa
     f.inv_dr = s.inv_dr_f;
     f.coef4 = (int)(s.tab_off >> 2);
     for (int j = 0; j < kMaxRadial; ++j) { f.rad_l[j] = j < s.n_radial ? s.rad_l[j] : 0; f.orb_base[j] = 0; }
-    for (int o = 0; o < kMaxNw; ++o) f.qe[o] = o < s.n_orb ? s.orb_qe[o] : 0;
+    for (int o = 0; o < kMaxNw; ++o) {
+        f.qe[o] = o < s.n_orb ? s.orb_qe[o] : 0;
+        f.qeu[o] = o < s.n_orb ? s.orb_qeu[o] : 0;
+    }
     // orbital order: l ascending, radial functions in input order, m = -l..l
     int o = 0;
     for (int l = 0; l <= kMaxL; ++l)
@@ -136,8 +140,10 @@ namespace gint {
 
 // Orbital values of one atom image at two points: put2(o, v0, v1) for every
 // orbital o; a point outside the cutoff contributes 0.  Returns false (no
-// calls) when both points are outside.  Same functions as orbitals_fast.
-template <typename Put2>
+// calls) when both points are outside.  Same functions as orbitals_fast; with
+// kNorm = false the harmonic normalisation ylm_norm(l, m) is left out (the
+// caller applies it in FP64).
+template <bool kNorm = true, typename Put2>
 __device__ __forceinline__ bool orbitals_fast2(const SpeciesFast& s, const float4* __restrict__ coef, float ax,
                                                float ay, float az, float bx, float by, float bz, Put2&& put2) {
     const float r2a = ax * ax + ay * ay + az * az;
@@ -152,10 +158,12 @@ __device__ __forceinline__ bool orbitals_fast2(const SpeciesFast& s, const float
     const float xa = ra * s.inv_dr, xb = rb * s.inv_dr;
     const int ka = min((int)xa, s.n_int - 1), kb = min((int)xb, s.n_int - 1);
     const float ta = xa - (float)ka, tb = xb - (float)kb;
-    const float k00 = 0.28209479177387814f, k1 = 0.48860251190291992f;
-    const float k2a = 1.0925484305920792f, k2b = 0.31539156525252005f, k2c = 0.54627421529603959f;
-    const float k3a = 0.59004358992664352f, k3b = 2.8906114426405538f, k3c = 0.45704579946446572f;
-    const float k3d = 0.37317633259011540f, k3e = 1.4453057213202769f;
+    const float k00 = kNorm ? 0.28209479177387814f : 1.f, k1 = kNorm ? 0.48860251190291992f : 1.f;
+    const float k2a = kNorm ? 1.0925484305920792f : 1.f, k2b = kNorm ? 0.31539156525252005f : 1.f;
+    const float k2c = kNorm ? 0.54627421529603959f : 1.f;
+    const float k3a = kNorm ? 0.59004358992664352f : 1.f, k3b = kNorm ? 2.8906114426405538f : 1.f;
+    const float k3c = kNorm ? 0.45704579946446572f : 1.f;
+    const float k3d = kNorm ? 0.37317633259011540f : 1.f, k3e = kNorm ? 1.4453057213202769f : 1.f;
     const float4* cfa = coef + s.coef4 + ka * s.n_radial;
     const float4* cfb = coef + s.coef4 + kb * s.n_radial;
     for (int j = 0; j < s.n_radial; ++j) {

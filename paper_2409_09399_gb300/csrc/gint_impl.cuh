@@ -41,7 +41,26 @@ struct SpeciesDev {
     signed char orb_l[kMaxNw];
     signed char orb_m[kMaxNw];    // m + l, 0..2l
     signed char orb_qe[kMaxNw];   // |phi_o(r)| <= 127 * 2^orb_qe for every r (fixed-point quantum)
+    signed char orb_qeu[kMaxNw];  // the same for phi_o / ylm_norm(l, m) (unnormalised harmonic)
 };
+
+// Normalisation of the real solid harmonics in the orbital definition:
+// phi_lm = R(r) / r^l * ylm_norm(l, m) * P_lm(x, y, z), with the polynomials
+// P: l = 1: y, z, x; l = 2: xy, yz, 2z^2 - x^2 - y^2, xz, x^2 - y^2;
+// l = 3: y(3x^2 - y^2), xyz, y(4z^2 - x^2 - y^2), z(2z^2 - 3x^2 - 3y^2),
+// x(4z^2 - x^2 - y^2), z(x^2 - y^2), x(x^2 - 3y^2)  (m = -l..l).
+__host__ __device__ inline double ylm_norm(int l, int mi) {  // mi = m + l
+    switch (l) {
+        case 0: return 0.28209479177387814;   // 1 / (2 sqrt(pi))
+        case 1: return 0.48860251190291992;   // sqrt(3 / (4 pi))
+        case 2: return (mi == 2) ? 0.31539156525252005 : (mi == 4) ? 0.54627421529603959 : 1.0925484305920792;
+        default: {
+            const double t[7] = {0.59004358992664352, 2.8906114426405538, 0.45704579946446572, 0.37317633259011540,
+                                 0.45704579946446572, 1.4453057213202769, 0.59004358992664352};
+            return t[mi];
+        }
+    }
+}
 
 // An atom image (I, T) whose cutoff sphere meets the grid.
 struct ExtAtom {
@@ -61,6 +80,7 @@ struct GridDev {
     int bpad;        // bpts rounded up to a multiple of 32
     int nsub;        // bpad / 32
     double step[3][3];  // step[i] = a_i / n_i
+    float step_hi[3][3], step_lo[3][3];  // step = hi + lo, FP32 words (in-brick offsets without a scale bias)
     double dV;
 };
 
@@ -127,10 +147,12 @@ struct gint_handle {
     int32_t* d_empty = nullptr;       // empty bricks
     int* d_err = nullptr;             // [0] device check flags, [2] work counter
     int* d_nw_atom = nullptr;         // orbitals of every atom
+    int* d_atom_sp = nullptr;         // species of every atom
     double* d_facc = nullptr;         // per-atom force and virial accumulators, n_atoms x 12
     double* d_red = nullptr;          // small FP64 reduction buffer ([0] energy)
     void* d_dt = nullptr;             // per-call 16x16 tensor-core copy of D (1 KB per block)
     int* d_dq = nullptr;              // exact form: per (atom, orbital row) max |D| bits, n_atoms x 16
+    void* d_zero = nullptr;           // one zero tile of the tensor-core copy of D
     void* d_scratch = nullptr;
     size_t scratch_bytes = 0;
     int n_ctas = 0;                   // persistent CTAs of the SIMT kernels

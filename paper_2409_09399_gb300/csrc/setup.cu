@@ -554,6 +554,9 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
             int e = 0;
             if (bound > 0.0) std::frexp(bound / 127.0, &e);  // bound / 127 < 2^e
             D.orb_qe[o] = (signed char)std::max(-100, std::min(100, e));
+            e = 0;
+            if (bound > 0.0) std::frexp(bound / ylm_norm(D.orb_l[o], D.orb_m[o]) / 127.0, &e);
+            D.orb_qeu[o] = (signed char)std::max(-100, std::min(100, e));
         }
         nw_sp[s] = norb;
         rc_sp[s] = S.rc;
@@ -600,7 +603,11 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
         g.B[i] = (opt && opt->brick[i] > 0) ? opt->brick[i] : Bdef[i];
         if (g.B[i] > g.n[i]) g.B[i] = g.n[i];
         g.nb[i] = (g.n[i] + g.B[i] - 1) / g.B[i];
-        for (int j = 0; j < 3; ++j) g.step[i][j] = cell[3 * i + j] / grid[i];
+        for (int j = 0; j < 3; ++j) {
+            g.step[i][j] = cell[3 * i + j] / grid[i];
+            g.step_hi[i][j] = (float)g.step[i][j];
+            g.step_lo[i][j] = (float)(g.step[i][j] - (double)g.step_hi[i][j]);
+        }
     }
     g.bpts = g.B[0] * g.B[1] * g.B[2];
     if (g.bpts > kMaxBrickPts) {
@@ -664,6 +671,7 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
         std::vector<int> nwa(n_atoms);
         for (int i = 0; i < n_atoms; ++i) nwa[i] = nw_sp[spc[i]];
         GINT_TRY(dev_upload(&h->d_nw_atom, nwa.data(), nwa.size()));
+        GINT_TRY(dev_upload(&h->d_atom_sp, spc.data(), spc.size()));
     }
     GINT_CUDA_TRY(cudaMalloc(&h->d_mirror, sizeof(int32_t) * std::max<int64_t>(1, h->n_blocks)));
     {
@@ -792,7 +800,7 @@ static void free_handle(gint_handle* h) {
     cudaSetDevice(h->device);
     void* ptrs[] = {h->d_sp, h->d_coef64, h->d_coef32, h->d_ext, h->d_blocks, h->d_offsets, h->d_row_start,
                     h->d_mirror, h->d_brick_start, h->d_brick_atoms, h->d_work, h->d_empty, h->d_err, h->d_red,
-                    h->d_scratch, h->d_nw_atom, h->d_facc, h->d_dt, h->d_dq};
+                    h->d_scratch, h->d_nw_atom, h->d_atom_sp, h->d_facc, h->d_dt, h->d_dq, h->d_zero};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (prev >= 0) cudaSetDevice(prev);

@@ -20,10 +20,12 @@
 // additions per element (96 per brick) the way a rounding biased towards zero
 // in the FP32 accumulator predicts, and the bias does not average out over the
 // bricks that add into one H element.  The exact form (fp16x4) avoids that
-// bias for the leading term: every operand value x of row (orbital) o is
-// written as x / q_o = n + l1 + l2 with q_o = 2^qe_o a per-orbital quantum
-// (|x| <= 127 q_o at every point), n = rint(x / q_o) an integer of at most 8
-// bits and l1, l2 two fp16 pieces of the remainder.  Products n_a n_b are
+// bias for the leading term: the orbital values are taken without the
+// harmonic normalisation (applied in FP64 in the epilogue, so that its FP32
+// rounding does not scale whole rows of H), and every operand value x of row
+// (orbital) o is written as x / q_o = n + l1 + l2 with q_o = 2^qe_o a
+// per-orbital quantum (|x| <= 127 q_o at every point), n = rint(x / q_o) an
+// integer of at most 8 bits and l1, l2 two fp16 pieces of the remainder.  Products n_a n_b are
 // integers below 2^14, so their sums over <= 512 points stay below 2^23 and
 // accumulate exactly in FP32; the cross terms n l1 + l1 n + l1 l1 + n l2 + l2 n
 // (2^-7 of the leading term) go to a second accumulator.  Each output column
@@ -79,6 +81,7 @@ struct TcAtom {
 struct TcArgs {
     Problem P;
     int* counter;
+    int norm_after;  // exact form: leave the harmonic normalisation to k_norm_h (H not accumulated into)
 };
 
 template <bool kExact> struct TcSmem {
@@ -91,7 +94,7 @@ template <bool kExact> struct TcSmem {
     unsigned char row_atom[C::kRows];
     unsigned char row_mu[C::kRows];
     unsigned short rowtab[C::kRows];  // byte offset of row r's 16-byte segment in a piece
-    float row_q[C::kRows];            // exact form: quantum 2^qe of row r
+    double row_s[C::kRows];           // exact form: [ylm_norm x] 2^qeu of row r (FP64)
     unsigned char seg_tile[kTcMaxSeg];  // segment: row tile, columns [c0, c1), TMEM column
     short seg_c0[kTcMaxSeg], seg_c1[kTcMaxSeg], seg_tcol[kTcMaxSeg];
     int pass_first[kTcMaxSeg + 1];      // first segment of each pass
@@ -173,6 +176,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
         S.abort = 0;
     }
     if (tid < P.n_species) species_fast_from(P.sp[tid], S.spf[tid]);
+    // in-brick point offsets (the same for every brick): FP64, rounded once to FP32
+    for (int p = tid; p < g.bpad && p < C::kPts; p += kTcThreads) {
+        const int l2 = p % g.B[2], l1 = (p / g.B[2]) % g.B[1], l0 = p / (g.B[2] * g.B[1]);
+        float4 q4;
+        q4.x = (float)(l0 * g.step[0][0] + l1 * g.step[1][0] + l2 * g.step[2][0]);
+        q4.y = (float)(l0 * g.step[0][1] + l1 * g.step[1][1] + l2 * g.step[2][1]);
+        q4.z = (float)(l0 * g.step[0][2] + l1 * g.step[1][2] + l2 * g.step[2][2]);
+        q4.w = 0.f;
+        S.pt[p] = q4;
+    }
     for (int r = tid; r < C::kRows; r += kTcThreads) S.rowtab[r] = (unsigned short)((((r >> 3) * (kTcChunk / 8)) << 7) + ((r & 7) << 4));
     tc::fence_before_sync();
     __syncthreads();
@@ -220,13 +233,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
             float wv = 0.f;
             if (brick_point(g, b0, b1, b2, p, g0, g1, g2))
                 wv = (float)(V[((int64_t)g0 * g.n[1] + g1) * g.n[2] + g2] * g.dV);
-            const int l2 = p % g.B[2], l1 = (p / g.B[2]) % g.B[1], l0 = p / (g.B[2] * g.B[1]);
-            float4 q4;
-            q4.x = (float)l0 * (float)g.step[0][0] + (float)l1 * (float)g.step[1][0] + (float)l2 * (float)g.step[2][0];
-            q4.y = (float)l0 * (float)g.step[0][1] + (float)l1 * (float)g.step[1][1] + (float)l2 * (float)g.step[2][1];
-            q4.z = (float)l0 * (float)g.step[0][2] + (float)l1 * (float)g.step[1][2] + (float)l2 * (float)g.step[2][2];
-            q4.w = p < g.bpts ? wv : 0.f;
-            S.pt[p] = q4;
+            S.pt[p].w = p < g.bpts ? wv : 0.f;
             wmax = fmaxf(wmax, fabsf(wv));
         }
         for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
@@ -242,10 +249,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
             for (int i = 0; i < na; ++i) {
                 S.at[i].off = off;
                 const SpeciesFast& sf = S.spf[S.at[i].sp];
+                const SpeciesDev& sd = P.sp[S.at[i].sp];
                 for (int o = 0; o < S.at[i].nw; ++o) {
                     S.row_atom[off + o] = (unsigned char)i;
                     S.row_mu[off + o] = (unsigned char)o;
-                    if (kExact) S.row_q[off + o] = exp2i(sf.qe[o]);
+                    if (kExact)
+                        S.row_s[off + o] = (A.norm_after ? 1.0 : ylm_norm(sd.orb_l[o], sd.orb_m[o])) * (double)exp2i(sf.qeu[o]);
                 }
                 off += S.at[i].nw;
             }
@@ -369,7 +378,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
                                 *reinterpret_cast<uint32_t*>(&buf[offB + pc * kBP]) = x0 | ((uint32_t)x1 << 16);
                             };
                             if (kExact) {
-                                const float qi = exp2i(-sf.qe[o]);
+                                const float qi = exp2i(-sf.qeu[o]);  // unnormalised orbital values
                                 va *= qi;
                                 vb *= qi;
                                 unsigned short n0, p0, r0, n1, p1, r1;
@@ -396,7 +405,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
                                 stB(0, bh0, bh1); stB(1, bl0, bl1);
                             }
                         };
-                        if (!orbitals_fast2(sf, coef4, ax, ay, az, bx, by, bz, put2))
+                        if (!orbitals_fast2<!kExact>(sf, coef4, ax, ay, az, bx, by, bz, put2))
                             for (int o = 0; o < X.nw; ++o) {
                                 const int r = rbase + o;
                                 const int offB = kBOff + S.rowtab[r] + qoff;
@@ -480,7 +489,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
                     const int a1 = rvalid ? S.row_atom[r] : 0;
                     const int mu = rvalid ? S.row_mu[r] : 0;
                     const int ngrp = (S.seg_c1[sg] - cs0) >> 4;
-                    const float qr = kExact && rvalid ? S.row_q[r] * sinv : sinv;
+                    const double qr = kExact && rvalid ? S.row_s[r] * (double)sinv : (double)sinv;
                     for (int gq = warp >> 2; gq < ngrp; gq += 4) {
                         float v[16], v1[16];
                         const uint32_t ta = tmem + ((uint32_t)lane_base << 16) + (uint32_t)(S.seg_tcol[sg] + 16 * gq);
@@ -497,9 +506,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
                             if (blk < 0) continue;
                             const int64_t off = __ldg(P.offsets + blk);
                             const int nu = S.row_mu[col];
-                            // scale factors are powers of two: exact
-                            const double val = kExact ? ((double)v[jj] + (double)v1[jj]) * (double)(qr * S.row_q[col])
-                                                      : (double)(v[jj] * sinv);
+                            // three-product form: power-of-two scale (exact); exact form: FP64 row and
+                            // column factors (harmonic normalisation x quantum) and 2^-s
+                            // with norm_after the factors are a power of two p2: the two accumulators are
+                            // added with an error-free FP32 two-sum, scaled exactly, and joined in FP64
+                            double val;
+                            if (!kExact) {
+                                val = (double)(v[jj] * sinv);
+                            } else if (A.norm_after) {
+                                const float p2 = (float)(qr * S.row_s[col]);
+                                const float a = v[jj], b = v1[jj];
+                                const float sm = a + b, bb = sm - a;
+                                const float er = (a - (sm - bb)) + (b - bb);
+                                val = (double)(sm * p2) + (double)(er * p2);
+                            } else {
+                                val = ((double)v[jj] + (double)v1[jj]) * (qr * S.row_s[col]);
+                            }
                             const int nw2 = S.at[a2].nw;
                             if (a1 == a2) {
                                 // same atom image: the block is symmetric; keep r <= col and mirror
@@ -531,6 +553,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
 
 template <bool kExact> size_t tc_smem_bytes() { return sizeof(TcSmem<kExact>) + 1024; }
 
+// Exact form: multiply every canonical H block by the harmonic normalisation of
+// its row and column orbitals (FP64, once per element rather than once per brick).
+__global__ void k_norm_h(Problem P, const int* atom_sp, int64_t n_blocks, double* H) {
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= n_blocks) return;
+    const int32_t* k = P.blocks + 5 * b;
+    const int I = k[0], J = k[1];
+    const bool canon = (I < J) || (I == J && (k[2] > 0 || (k[2] == 0 && (k[3] > 0 || (k[3] == 0 && k[4] >= 0)))));
+    if (!canon) return;
+    const SpeciesDev& si = P.sp[atom_sp[I]];
+    const SpeciesDev& sj = P.sp[atom_sp[J]];
+    const int nI = si.n_orb, nJ = sj.n_orb;
+    double* Hb = H + P.offsets[b];
+    for (int e = lane; e < nI * nJ; e += 32) {
+        const int mu = e / nJ, nu = e - mu * nJ;
+        Hb[e] *= ylm_norm(si.orb_l[mu], si.orb_m[mu]) * ylm_norm(sj.orb_l[nu], sj.orb_m[nu]);
+    }
+}
+
 // form: 0 = fp16x3, 1 = bf16x3, 2 = fp16x4 (exact leading term)
 gint_status tc_vlocal_check(const gint_handle* h, int form) {
     const bool exact = form == 2;
@@ -546,11 +588,12 @@ gint_status tc_vlocal_check(const gint_handle* h, int form) {
     return GINT_OK;
 }
 
-gint_status tc_vlocal(gint_handle* h, int form, const double* V, double* H, cudaStream_t st) {
+gint_status tc_vlocal(gint_handle* h, int form, const double* V, double* H, int accumulate, cudaStream_t st) {
     gint_status s = tc_vlocal_check(h, form);
     if (s != GINT_OK || h->n_work == 0) return s;
     const bool exact = form == 2;
     TcArgs A;
+    A.norm_after = exact && !accumulate ? 1 : 0;
     A.P = h->problem();
     A.counter = h->d_err + 2;
     GINT_CUDA_TRY(cudaMemsetAsync(A.counter, 0, sizeof(int), st));
@@ -566,6 +609,10 @@ gint_status tc_vlocal(gint_handle* h, int form, const double* V, double* H, cuda
     else GINT_LAUNCH_VL(__half, false);
 #undef GINT_LAUNCH_VL
     GINT_CUDA_TRY(cudaGetLastError());
+    if (A.norm_after && h->n_blocks > 0) {
+        k_norm_h<<<(unsigned)((h->n_blocks * 32 + 255) / 256), 256, 0, st>>>(A.P, h->d_atom_sp, h->n_blocks, H);
+        GINT_CUDA_TRY(cudaGetLastError());
+    }
     return GINT_OK;
 }
 

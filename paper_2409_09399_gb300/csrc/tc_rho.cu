@@ -38,7 +38,8 @@
 namespace gint {
 
 namespace {
-constexpr int kThreads = 256;
+constexpr int kProdWarps = 8;                    // orbital-value producers and epilogue
+constexpr int kThreads = 32 * kProdWarps + 32;   // + one warp for B copies and MMA issue
 constexpr int kMaxAtoms = 64;
 constexpr int kMaxCols = 512;            // TMEM columns (packed orbitals of one M-tile)
 // A pieces (128 points x 16 orbital slots) are MN-major: core matrix (point group
@@ -80,9 +81,11 @@ template <bool kExact> struct Smem {
     float rho_half[128];                 // partial rho from warps 4-7
     SpeciesFast spf[kMaxSpecies];
     unsigned char act[kMaxAtoms];
-    int rowoff[kMaxAtoms + 1];
     unsigned long long active_mask;
-    uint64_t bar[2];
+    uint64_t full[2];    // producers wrote A of buffer b (256 arrivals)
+    uint64_t empty[2];   // MMAs reading buffer b completed (tcgen05.commit)
+    uint64_t bfull[2];   // bulk copies of B into buffer b completed
+    uint64_t done;       // all MMAs of a column group completed
     uint32_t tmem;
     int work, abort, nact, ncols;
 };
@@ -146,10 +149,15 @@ __device__ __forceinline__ int warp_sum16_index(int lane) {
 }
 
 __device__ __forceinline__ void point_offset(const GridDev& g, int p, float& fx, float& fy, float& fz) {
+    // step = hi + lo (FP32 words): the offset carries rounding errors only, no scale error of the step
     const int l2 = p % g.B[2], l1 = (p / g.B[2]) % g.B[1], l0 = p / (g.B[2] * g.B[1]);
-    fx = (float)l0 * (float)g.step[0][0] + (float)l1 * (float)g.step[1][0] + (float)l2 * (float)g.step[2][0];
-    fy = (float)l0 * (float)g.step[0][1] + (float)l1 * (float)g.step[1][1] + (float)l2 * (float)g.step[2][1];
-    fz = (float)l0 * (float)g.step[0][2] + (float)l1 * (float)g.step[1][2] + (float)l2 * (float)g.step[2][2];
+    const float f0 = (float)l0, f1 = (float)l1, f2 = (float)l2;
+    fx = (f0 * g.step_hi[0][0] + f1 * g.step_hi[1][0] + f2 * g.step_hi[2][0]) +
+         (f0 * g.step_lo[0][0] + f1 * g.step_lo[1][0] + f2 * g.step_lo[2][0]);
+    fy = (f0 * g.step_hi[0][1] + f1 * g.step_hi[1][1] + f2 * g.step_hi[2][1]) +
+         (f0 * g.step_lo[0][1] + f1 * g.step_lo[1][1] + f2 * g.step_lo[2][1]);
+    fz = (f0 * g.step_hi[0][2] + f1 * g.step_hi[1][2] + f2 * g.step_hi[2][2]) +
+         (f0 * g.step_lo[0][2] + f1 * g.step_lo[1][2] + f2 * g.step_lo[2][2]);
 }
 }  // namespace
 
@@ -217,8 +225,8 @@ __global__ void k_format_d(Problem P, const int32_t* mirror, const int* nw_atom,
 
 template <typename H16, bool kForce, bool kExact>
 __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* counter, const double* V,
-                                                            const unsigned char* Dt, const int* dq, double* rho,
-                                                            double* facc, double* acc_e) {
+                                                            const unsigned char* Dt, const unsigned char* Dzero,
+                                                            const int* dq, double* rho, double* facc, double* acc_e) {
     constexpr int kCols = kExact ? kMaxCols / 2 : kMaxCols;  // output columns of one column group
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem<kExact>& S = *reinterpret_cast<Smem<kExact>*>(smem_raw);
@@ -232,8 +240,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(&S.bar[0], 1);
-        tc::mbar_init(&S.bar[1], 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&S.full[b], 32 * kProdWarps);
+            tc::mbar_init(&S.empty[b], 1);
+            tc::mbar_init(&S.bfull[b], 1);
+        }
+        tc::mbar_init(&S.done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         S.abort = 0;
     }
@@ -248,7 +260,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
         for (int sp = 0; sp < P.n_species; ++sp)
             for (int o = 0; o < S.spf[sp].nw; ++o) qa = max(qa, (int)S.spf[sp].qe[o]);
     const float qa_inv = kExact ? exp2f_i(-qa) : 1.f, qa_f = kExact ? exp2f_i(qa) : 1.f;
-    uint32_t commits[2] = {0, 0};
+    uint32_t uses[2] = {0, 0};  // steps that used buffer b (every thread counts them)
+    uint32_t dones = 0;         // completed phases of done
+    uint32_t bissue[2] = {0, 0}, bdone[2] = {0, 0};  // warp 8 lane 0: bulk-copy phases started / waited
     uint32_t chunk = 0;  // global chunk counter (buffer parity)
     const float4* coef4 = reinterpret_cast<const float4*>(P.coef32);
 
@@ -330,15 +344,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
             }
             __syncthreads();
             if (tid == 0) {
-                int n = 0, off = 0;
+                int n = 0;
                 for (int a = 0; a < na; ++a)
-                    if (S.active_mask >> a & 1ull) {
-                        S.act[n] = (unsigned char)a;
-                        S.rowoff[n] = off;
-                        off += S.at[a].nw;
-                        ++n;
-                    }
-                S.rowoff[n] = off;
+                    if (S.active_mask >> a & 1ull) S.act[n++] = (unsigned char)a;
                 S.nact = n;
             }
             __syncthreads();
@@ -352,51 +360,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
                 continue;
             }
             if (S.abort) break;
-            // column groups: consecutive active images whose orbitals fit the 512 TMEM columns
+            // column groups: consecutive active images, one 16-column slot each (a slot holds
+            // an image's <= 16 orbitals, zero padded), at most kCols / 16 images per group
             for (int cg0 = 0; cg0 < nact && !S.abort;) {
-            int cg1 = cg0;
-            while (cg1 < nact && S.rowoff[cg1 + 1] - S.rowoff[cg0] <= kCols) ++cg1;
-            if (cg1 == cg0) cg1 = cg0 + 1;  // never taken (an image has <= 16 orbitals); keeps the loop finite
-            const int rbase = S.rowoff[cg0];
-            const int nrows = S.rowoff[cg1] - rbase;
-            const int ncols = (nrows + 15) & ~15;
-            // zero B padding rows [nrows, ncols) of both buffers (MMAs of earlier tiles are complete)
-            for (int e = tid; e < (ncols - nrows) * 2; e += kThreads) {
-                const int r = nrows + (e >> 1), half = e & 1;
-                for (int b = 0; b < 2; ++b)
-                    for (int j = 0; j < 2; ++j)
-                        for (int pc = 0; pc < C::kPieces; ++pc)
-                            *reinterpret_cast<uint4*>(&S.B[b][j][pc * kBPiece + kmaj16(r, half * 8)]) = make_uint4(0, 0, 0, 0);
-            }
-            // ---- K loop over active images, two images (K = 32) per step
-            for (int k = 0; k < nact; k += 2, ++chunk) {
-                const int b = chunk & 1;
-                const int nk = min(2, nact - k);
-                if (commits[b] > 0 && !tc::mbar_wait(&S.bar[b], (commits[b] - 1) & 1, kWait))
-                    if (lane == 0) atomicOr(&S.abort, 1);
-                // B rows (asynchronous copies first): for image a1 = act[k + j] and every active
-                // image a2 of the group, rows nu of block (I_a2, I_a1, T_a1 - T_a2)
-                constexpr int kParts = 2 * C::kPieces;  // (piece, half) per B row
-                for (int e = tid; e < nk * nrows * kParts; e += kThreads) {
-                    const int j = e / (nrows * kParts), rem = e - j * nrows * kParts;
-                    const int r = rem / kParts, part = rem - r * kParts;
-                    int lo_j = cg0, hi_j = cg1 - 1;
-                    while (lo_j < hi_j) {
-                        const int mid = (lo_j + hi_j + 1) >> 1;
-                        if (S.rowoff[mid] <= rbase + r) lo_j = mid; else hi_j = mid - 1;
-                    }
-                    const int a2 = S.act[lo_j];
-                    const int nu = rbase + r - S.rowoff[lo_j];
-                    const int blk = S.pairblk[S.act[k + j] * na + a2];
-                    const int pc = part >> 1, half = part & 1;
-                    unsigned char* dst = &S.B[b][j][pc * kBPiece + kmaj16(r, half * 8)];
-                    if (blk >= 0) tc::cp_async16(dst, Dt + (int64_t)blk * kDtBytes + pc * kDtPiece + kmaj16(nu, half * 8));
-                    else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
-                }
-                // A rows: orbital values of image act[k + j] at point p (16 slots, zero padded)
-                {
-                    const int j = tid >> 7, pl = tid & 127;
-                    if (j < nk) {
+            const int cg1 = min(nact, cg0 + kCols / 16);
+            const int ncols = 16 * (cg1 - cg0);
+            // ---- K loop over active images, two images (K = 32) per step.  Warps 0-7 produce
+            // A (orbital values of the step's two K images at the tile's 128 points) into
+            // buffer b = step & 1 and arrive on full[b]; warp 8 fetches B and lane 0 of it
+            // issues the MMAs of a step once full[b] and bfull[b] complete, then commits
+            // empty[b].  B (bulk asynchronous copies by warp 8): for K image a1 = act[k + j]
+            // and the image a2 in slot s of the group, the pre-formatted tile of block
+            // (I_a2, I_a1, T_a1 - T_a2) (a zero tile when the pair has no block), 512 B per
+            // piece, is exactly the slot's 16-byte rows in the K-major B layout; the copies
+            // of step s + 1 start right after the MMAs of step s are issued.
+            const int nsteps = (nact + 1) >> 1;
+            if (warp < kProdWarps) {
+                const int j = tid >> 7, pl = tid & 127;
+                for (int st = 0; st < nsteps; ++st) {
+                    const int b = (chunk + st) & 1, k = 2 * st;
+                    const int nk = min(2, nact - k);
+                    if (uses[b] > 0 && !tc::mbar_wait(&S.empty[b], (uses[b] - 1) & 1, kWait)) atomicOr(&S.abort, 1);
+                    if (j < nk && !S.abort) {
                         const Atom& X = S.at[S.act[k + j]];
                         const int p = mt * 128 + pl;
                         unsigned char* A0 = S.A[b][j];
@@ -425,46 +410,79 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
                                 for (int pc = 0; pc < C::kPieces; ++pc)
                                     *reinterpret_cast<unsigned short*>(A0 + pc * kAPiece + amn(pl, o)) = 0;
                     }
+                    tc::fence_async_smem();
+                    tc::mbar_arrive(&S.full[b]);
+                    uses[b] += 1;
                 }
-                tc::cp_async_wait_all();
-                tc::fence_async_smem();
-                __syncthreads();
-                if (S.abort) break;
-                if (tid == 0) {
-                    tc::fence_after_sync();
-                    for (int j = 0; j < nk; ++j) {
-                        const uint32_t a_hi = tc::smem_u32(S.A[b][j]), a_lo = a_hi + kAPiece, a_l2 = a_lo + kAPiece;
-                        const uint32_t bb = tc::smem_u32(S.B[b][j]);
-                        for (int n0 = 0; n0 < ncols; n0 += 256) {
-                            const int nn = min(256, ncols - n0);
-                            const uint32_t idesc = tc::idesc_f16(128, nn, Split<H16>::bf16, 1, 0);  // A MN-major
-                            const uint32_t b_hi = bb + (n0 >> 3) * 256, b_lo = b_hi + kBPiece, b_l2 = b_lo + kBPiece;
-                            const uint32_t d = tmem + (uint32_t)n0;
-                            // B K-major with 16 K-columns: LBO (K-adjacent cores) 128 B, SBO (row groups) 256 B;
-                            // A MN-major: LBO (orbital groups) kALbo, SBO (point groups) kASbo
-                            const uint32_t acc = (k + j) > 0 ? 1u : 0u;
-                            tc::mma_f16(d, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_hi, 128, 256), idesc, acc);
-                            if (kExact) {
-                                const uint32_t d1 = d + kCols;  // cross terms
-                                tc::mma_f16(d1, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_lo, 128, 256), idesc, acc);
-                                tc::mma_f16(d1, tc::smem_desc(a_lo, kALbo, kASbo), tc::smem_desc(b_hi, 128, 256), idesc, 1u);
-                                tc::mma_f16(d1, tc::smem_desc(a_lo, kALbo, kASbo), tc::smem_desc(b_lo, 128, 256), idesc, 1u);
-                                tc::mma_f16(d1, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_l2, 128, 256), idesc, 1u);
-                                tc::mma_f16(d1, tc::smem_desc(a_l2, kALbo, kASbo), tc::smem_desc(b_hi, 128, 256), idesc, 1u);
-                            } else {
-                                tc::mma_f16(d, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_lo, 128, 256), idesc, 1u);
-                                tc::mma_f16(d, tc::smem_desc(a_lo, kALbo, kASbo), tc::smem_desc(b_hi, 128, 256), idesc, 1u);
+            } else {
+                // warp 8: B copies (all lanes) and MMA issue (lane 0)
+                auto issue_b = [&](int st) {
+                    const int bb = (chunk + st) & 1, kk = 2 * st;
+                    const int nkk = min(2, nact - kk);
+                    if (lane == 0) {
+                        if (uses[bb] > 0 && !tc::mbar_wait(&S.empty[bb], (uses[bb] - 1) & 1, kWait)) atomicOr(&S.abort, 1);
+                        tc::mbar_arrive_expect_tx(&S.bfull[bb], (uint32_t)(nkk * (cg1 - cg0) * C::kPieces * kDtPiece));
+                        bissue[bb] += 1;
+                    }
+                    __syncwarp();
+                    const int per_img = (cg1 - cg0) * C::kPieces;
+                    for (int e = lane; e < nkk * per_img; e += 32) {
+                        const int jj = e / per_img, rem = e - jj * per_img;
+                        const int sl = rem / C::kPieces, pc = rem - sl * C::kPieces;
+                        const int blk = S.pairblk[S.act[kk + jj] * na + S.act[cg0 + sl]];
+                        const unsigned char* src = blk >= 0 ? Dt + (int64_t)blk * kDtBytes : Dzero;
+                        tc::bulk_copy_g2s(&S.B[bb][jj][pc * kBPiece + sl * kDtPiece], src + pc * kDtPiece, kDtPiece,
+                                          &S.bfull[bb]);
+                    }
+                };
+                issue_b(0);
+                for (int st = 0; st < nsteps; ++st) {
+                    const int b = (chunk + st) & 1, k = 2 * st;
+                    const int nk = min(2, nact - k);
+                    if (lane == 0) {
+                        if (!S.abort && !tc::mbar_wait(&S.full[b], uses[b] & 1, kWait)) atomicOr(&S.abort, 1);
+                        if (!S.abort) {
+                            if (tc::mbar_wait(&S.bfull[b], uses[b] & 1, kWait)) bdone[b] += 1;
+                            else atomicOr(&S.abort, 1);
+                        }
+                        tc::fence_after_sync();
+                        for (int jm = 0; jm < nk && !S.abort; ++jm) {
+                            const uint32_t a_hi = tc::smem_u32(S.A[b][jm]), a_lo = a_hi + kAPiece, a_l2 = a_lo + kAPiece;
+                            const uint32_t bb = tc::smem_u32(S.B[b][jm]);
+                            for (int n0 = 0; n0 < ncols; n0 += 256) {
+                                const int nn = min(256, ncols - n0);
+                                const uint32_t idesc = tc::idesc_f16(128, nn, Split<H16>::bf16, 1, 0);  // A MN-major
+                                const uint32_t b_hi = bb + (n0 >> 3) * 256, b_lo = b_hi + kBPiece, b_l2 = b_lo + kBPiece;
+                                const uint32_t d = tmem + (uint32_t)n0;
+                                // B K-major with 16 K-columns: LBO (K-adjacent cores) 128 B, SBO (row groups) 256 B;
+                                // A MN-major: LBO (orbital groups) kALbo, SBO (point groups) kASbo
+                                const uint32_t acc = (k + jm) > 0 ? 1u : 0u;
+                                tc::mma_f16(d, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_hi, 128, 256), idesc, acc);
+                                if (kExact) {
+                                    const uint32_t d1 = d + kCols;  // cross terms
+                                    tc::mma_f16(d1, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_lo, 128, 256), idesc, acc);
+                                    tc::mma_f16(d1, tc::smem_desc(a_lo, kALbo, kASbo), tc::smem_desc(b_hi, 128, 256), idesc, 1u);
+                                    tc::mma_f16(d1, tc::smem_desc(a_lo, kALbo, kASbo), tc::smem_desc(b_lo, 128, 256), idesc, 1u);
+                                    tc::mma_f16(d1, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_l2, 128, 256), idesc, 1u);
+                                    tc::mma_f16(d1, tc::smem_desc(a_l2, kALbo, kASbo), tc::smem_desc(b_hi, 128, 256), idesc, 1u);
+                                } else {
+                                    tc::mma_f16(d, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_lo, 128, 256), idesc, 1u);
+                                    tc::mma_f16(d, tc::smem_desc(a_lo, kALbo, kASbo), tc::smem_desc(b_hi, 128, 256), idesc, 1u);
+                                }
                             }
                         }
+                        tc::mma_commit(&S.empty[b]);
+                        if (st + 1 == nsteps) tc::mma_commit(&S.done);
                     }
-                    tc::mma_commit(&S.bar[b]);
+                    __syncwarp();
+                    uses[b] += 1;
+                    if (st + 1 < nsteps) issue_b(st + 1);
                 }
-                commits[b] += 1;
             }
-            // ---- all MMAs of this tile complete
-            for (int b = 0; b < 2; ++b)
-                if (commits[b] > 0 && !tc::mbar_wait(&S.bar[b], (commits[b] - 1) & 1, kWait))
-                    if (lane == 0) atomicOr(&S.abort, 1);
+            chunk += nsteps;
+            // ---- all MMAs of this group complete (every thread waits on done)
+            if (!tc::mbar_wait(&S.done, dones & 1, kWait)) atomicOr(&S.abort, 1);
+            dones += 1;
             tc::fence_after_sync();
             if (kForce) {
                 for (int e = tid; e < kMaxAtoms * 13; e += kThreads) (&S.red[0][0])[e] = 0.0;
@@ -481,12 +499,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
                 float fx = 0.f, fy = 0.f, fz = 0.f;
                 if (p < g.bpts) point_offset(g, p, fx, fy, fz);
                 float rho_p = (cg0 == 0 || warp >= 4) ? 0.f : S.rho_part[pl];
-                for (int j = cg0 + (warp >> 2); j < cg1; j += 2) {
+                for (int j = cg0 + (warp >> 2); warp < kProdWarps && j < cg1; j += 2) {
                     const int a2 = S.act[j];
                     const Atom& Y = S.at[a2];
-                    int c0 = S.rowoff[j] - rbase;
-                    int sh = 0;
-                    if (c0 + 16 > kCols) { sh = c0 + 16 - kCols; c0 -= sh; }
+                    const int c0 = 16 * (j - cg0);  // the image's slot
+                    constexpr int sh = 0;
                     float Gv[16];
                     const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
                     tc::tmem_ld16(ta, Gv);
@@ -537,7 +554,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
                         if (!(lane & 1) && q < 13) atomicAdd(&S.red[j][q], (double)tot);
                     }
                 }
-                if (warp >= 4) S.rho_half[pl] = rho_p;
+                if (warp >= 4 && warp < kProdWarps) S.rho_half[pl] = rho_p;
                 tc::fence_before_sync();
                 __syncthreads();
                 if (warp < 4) {
@@ -563,8 +580,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
         __syncthreads();
     }
     __syncthreads();
-    for (int b = 0; b < 2; ++b)
-        if (commits[b] > 0) (void)tc::mbar_wait(&S.bar[b], (commits[b] - 1) & 1, kWait);
+    // no MMA or bulk copy may be in flight when tensor memory and shared memory are released:
+    // one more commit (completes after every earlier MMA) and the copies not yet waited for
+    if (warp == kProdWarps && lane == 0) {
+        tc::mma_commit(&S.done);
+        (void)tc::mbar_wait(&S.done, dones & 1, kWait);
+        for (int b = 0; b < 2; ++b)
+            if (bissue[b] > bdone[b]) (void)tc::mbar_wait(&S.bfull[b], bdone[b] & 1, kWait);
+    }
     if (S.abort && tid == 0) atomicOr(P.err, kErrTimeout);
     tc::fence_before_sync();
     __syncthreads();
@@ -578,6 +601,10 @@ static gint_status ensure_dt(gint_handle* h) {
         GINT_CUDA_TRY(cudaMalloc(&h->d_dt, bytes));
     }
     if (!h->d_dq) GINT_CUDA_TRY(cudaMalloc(&h->d_dq, sizeof(int) * 16 * (size_t)std::max(1, h->n_atoms)));
+    if (!h->d_zero) {  // a zero D tile for atom-image pairs without a block
+        GINT_CUDA_TRY(cudaMalloc(&h->d_zero, kDtBytes));
+        GINT_CUDA_TRY(cudaMemset(h->d_zero, 0, kDtBytes));
+    }
     return GINT_OK;
 }
 
@@ -633,7 +660,7 @@ gint_status tc_rhoforce(gint_handle* h, int form, bool force, const double* V, c
     do {                                                                                                        \
         GINT_CUDA_TRY(cudaFuncSetAttribute(k_rhoforce_tc<H16, F, X>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                            (int)smem));                                                         \
-        k_rhoforce_tc<H16, F, X><<<h->sm_count, kThreads, smem, st>>>(P, counter, V, Dt, h->d_dq, rho, facc, acc_e); \
+        k_rhoforce_tc<H16, F, X><<<h->sm_count, kThreads, smem, st>>>(P, counter, V, Dt, (const unsigned char*)h->d_zero, h->d_dq, rho, facc, acc_e); \
     } while (0)
     if (form == 1) {
         if (force) GINT_LAUNCH_RF(__nv_bfloat16, true, false); else GINT_LAUNCH_RF(__nv_bfloat16, false, false);

@@ -127,3 +127,19 @@ def test_tc_rho_force_tbg_sampled(precision, cuda):
     print(f"{precision} TBG m=2: rho normwise {e_rho:.3e}  F abs {e_F:.3e} (max {np.abs(F_ref).max():.3f})")
     assert e_rho < TOL[precision]["rho"]
     assert e_F < TOL[precision]["F"]
+
+
+def test_tc_exact_accumulate(cuda):
+    """Exact form with accumulate = 1 (normalisation in the FP64 epilogue) adds the same H."""
+    import torch
+    from paper_2409_09399_gb300 import gint
+    s, o, V, H_ref = diamond_case()
+    g = gint.from_system(s, precision="fp16x4", brick=(3, 3, 4))
+    Vt = torch.from_numpy(V).cuda()
+    H1 = g.vlocal(Vt)
+    H2 = g.vlocal(Vt, H=H1.clone(), accumulate=True)
+    g.sync()
+    e_acc = float((H2 - 2 * H1).abs().max())
+    e_ref = float(np.max(np.abs(H2.cpu().numpy() - 2 * H_ref)))
+    print(f"fp16x4 accumulate: |H2 - 2 H1| {e_acc:.2e}, |H2 - 2 H_ref| {e_ref:.2e}")
+    assert e_acc < 1e-7 and e_ref < 2e-7
