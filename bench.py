@@ -363,7 +363,16 @@ def run_ours(args):
     tpath = os.path.join(ROOT, "profiles", f"traffic_{dom_name}_{prec}.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
-            traffic = json.load(f).get("bytes_per_launch")
+            tj = json.load(f)
+        # DRAM bytes from an ncu capture, valid only while the kernel sources it was taken on are unchanged
+        import hashlib
+        hs = hashlib.sha256()
+        for src in tj.get("sources", []):
+            with open(os.path.join(ROOT, src), "rb") as f:
+                hs.update(f.read())
+        if tj.get("workload_scaled_to", tj.get("scaled_to", {}).get("workload")) == args.workload and \
+                hs.hexdigest() == tj.get("source_sha256"):
+            traffic = tj.get("bytes_per_launch")
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": dom_name, "peak_source": src,
             "algorithmic_flop_per_launch": flops[dom_name]}
