@@ -38,6 +38,12 @@ bool is_tc(const gint_handle* h) {
     return h->precision == GINT_BF16X3 || h->precision == GINT_FP16X3 || h->precision == GINT_FP16X4;
 }
 int tc_form(const gint_handle* h) { return h->precision == GINT_BF16X3 ? 1 : h->precision == GINT_FP16X4 ? 2 : 0; }
+}  // namespace
+
+// Tensor-core form of a handle's precision (0 fp16x3, 1 bf16x3, 2 fp16x4), -1 for the SIMT forms.
+int tc_form_of(const gint_handle* h) { return is_tc(h) ? tc_form(h) : -1; }
+
+namespace {
 
 gint_status check_precision(const gint_handle* h, bool* fp32) {
     if (h->precision == GINT_FP64) { *fp32 = false; return GINT_OK; }

@@ -1,11 +1,15 @@
 // fast_orb.cuh -- FP32 orbital values (and gradients) for the tensor-core
-// producers: no per-orbital local arrays, species data in shared memory, one
-// 16-byte table load per radial function, each orbital handed to a callback
-// as soon as it is formed.
+// producers: no per-orbital local arrays, species data in shared memory, the
+// radial data of two adjacent knots per radial function from a compact FP32
+// knot table, each orbital handed to a callback as soon as it is formed.
 //
-// phi_{l m}(d) = u(r) S_lm(d), u = R(r) / r^l, with R the cubic on the knot
-// interval (R = c0 + t (c1 + t (c2 + t c3)), t = r/dr - k) and S_lm the real
-// solid harmonics (normalised Y_lm, no Condon-Shortley phase).
+// phi_{l m}(d) = u(r) S_lm(d), u = R(r) / r^l, with R the cubic Hermite
+// interpolant on the knot interval [k, k+1] (t = r/dr - k):
+//   R = y_k h00(t) + y_k+1 h01(t) + m_k h10(t) + m_k+1 h11(t),  m = dr R'(knot),
+// the same cubic as the oracle's, and S_lm the real solid harmonics
+// (normalised Y_lm, no Condon-Shortley phase).  The knot table holds
+// (y_k, m_k) as two FP32 words per knot and radial function: half the bytes of
+// a per-interval power-basis table, so that more of it stays in L1.
 // grad phi = u'(r) (d / r) S_lm + u grad S_lm, u' = (R' - l R / r) / r^l.
 #pragma once
 
@@ -20,7 +24,7 @@ struct SpeciesFast {
     int nw;
     float rc2;
     float inv_dr;
-    int coef4;            // offset of the species' table in float4 units
+    int knot2;            // offset of the species' knot table in float2 units
     int rad_l[kMaxRadial];
     int orb_base[kMaxRadial];  // first orbital of each radial function
     signed char qe[kMaxNw];    // fixed-point quantum exponent of each orbital (|phi| <= 127 * 2^qe)
@@ -34,7 +38,7 @@ __device__ __forceinline__ void species_fast_from(const SpeciesDev& s, SpeciesFa
     f.nw = s.n_orb;
     f.rc2 = s.rc_f * s.rc_f;
     f.inv_dr = s.inv_dr_f;
-    f.coef4 = (int)(s.tab_off >> 2);
+    f.knot2 = (int)s.knot_off;
     for (int j = 0; j < kMaxRadial; ++j) { f.rad_l[j] = j < s.n_radial ? s.rad_l[j] : 0; f.orb_base[j] = 0; }
     for (int o = 0; o < kMaxNw; ++o) {
         f.qe[o] = o < s.n_orb ? s.orb_qe[o] : 0;
@@ -51,7 +55,7 @@ __device__ __forceinline__ void species_fast_from(const SpeciesDev& s, SpeciesFa
 // displacement d (the gradient arguments are meaningful only with kGrad);
 // returns false (no calls) when |d| >= rc.
 template <bool kGrad, typename Put>
-__device__ __forceinline__ bool orbitals_fast(const SpeciesFast& s, const float4* __restrict__ coef, float dx,
+__device__ __forceinline__ bool orbitals_fast(const SpeciesFast& s, const float2* __restrict__ knot, float dx,
                                               float dy, float dz, Put&& put) {
     const float r2 = dx * dx + dy * dy + dz * dz;
     if (r2 >= s.rc2) return false;
@@ -68,14 +72,19 @@ __device__ __forceinline__ bool orbitals_fast(const SpeciesFast& s, const float4
     const float k2a = 1.0925484305920792f, k2b = 0.31539156525252005f, k2c = 0.54627421529603959f;
     const float k3a = 0.59004358992664352f, k3b = 2.8906114426405538f, k3c = 0.45704579946446572f;
     const float k3d = 0.37317633259011540f, k3e = 1.4453057213202769f;
-    const float4* cf = coef + s.coef4 + k * s.n_radial;
+    // cubic Hermite basis at t and (for the gradient) its t-derivative
+    const float t1 = 1.f - t, tt = t * t;
+    const float h00 = (1.f + 2.f * t) * t1 * t1, h10 = t * t1 * t1, h01 = tt * (3.f - 2.f * t), h11 = tt * (t - 1.f);
+    const float g00 = 6.f * t * (t - 1.f), g10 = t1 * (1.f - 3.f * t), g11 = t * (3.f * t - 2.f);
+    const float2* kn = knot + s.knot2 + k * s.n_radial;
     for (int j = 0; j < s.n_radial; ++j) {
-        const float4 c = __ldg(cf + j);
+        const float2 y0 = __ldg(kn + j), y1 = __ldg(kn + s.n_radial + j);  // (R, dr R') at knots k, k + 1
         const int l = s.rad_l[j];
         const int o = s.orb_base[j];
-        float R = c.x + t * (c.y + t * (c.z + t * c.w));
+        float R = y0.x * h00 + y1.x * h01 + y0.y * h10 + y1.y * h11;
         float dR = 0.f;
-        if (kGrad) dR = (c.y + t * (2.f * c.z + t * (3.f * c.w))) * s.inv_dr;
+        if (kGrad) dR = ((y0.x - y1.x) * g00 + y0.y * g10 + y1.y * g11) * s.inv_dr;
+        const float4 c = make_float4(y0.x, y0.y, 0.f, 0.f);  // c.y = dr R'(0) at the first knot
         if (tiny) {
             // limits at the atom centre: phi = R(0) Y00 for l = 0, zero for l >= 1;
             // grad phi = R'(0) grad S_1m for l = 1, zero otherwise (c.y / dr = R'(0))
@@ -144,7 +153,7 @@ namespace gint {
 // kNorm = false the harmonic normalisation ylm_norm(l, m) is left out (the
 // caller applies it in FP64).
 template <bool kNorm = true, typename Put2>
-__device__ __forceinline__ bool orbitals_fast2(const SpeciesFast& s, const float4* __restrict__ coef, float ax,
+__device__ __forceinline__ bool orbitals_fast2(const SpeciesFast& s, const float2* __restrict__ knot, float ax,
                                                float ay, float az, float bx, float by, float bz, Put2&& put2) {
     const float r2a = ax * ax + ay * ay + az * az;
     const float r2b = bx * bx + by * by + bz * bz;
@@ -164,14 +173,18 @@ __device__ __forceinline__ bool orbitals_fast2(const SpeciesFast& s, const float
     const float k3a = kNorm ? 0.59004358992664352f : 1.f, k3b = kNorm ? 2.8906114426405538f : 1.f;
     const float k3c = kNorm ? 0.45704579946446572f : 1.f;
     const float k3d = kNorm ? 0.37317633259011540f : 1.f, k3e = kNorm ? 1.4453057213202769f : 1.f;
-    const float4* cfa = coef + s.coef4 + ka * s.n_radial;
-    const float4* cfb = coef + s.coef4 + kb * s.n_radial;
+    const float sa = 1.f - ta, qa2 = ta * ta, sb = 1.f - tb, qb2 = tb * tb;
+    const float a00 = (1.f + 2.f * ta) * sa * sa, a10 = ta * sa * sa, a01 = qa2 * (3.f - 2.f * ta), a11 = qa2 * (ta - 1.f);
+    const float b00 = (1.f + 2.f * tb) * sb * sb, b10 = tb * sb * sb, b01 = qb2 * (3.f - 2.f * tb), b11 = qb2 * (tb - 1.f);
+    const float2* kna = knot + s.knot2 + ka * s.n_radial;
+    const float2* knb = knot + s.knot2 + kb * s.n_radial;
     for (int j = 0; j < s.n_radial; ++j) {
-        const float4 ca = __ldg(cfa + j), cb = __ldg(cfb + j);
+        const float2 pa = __ldg(kna + j), qa = __ldg(kna + s.n_radial + j);
+        const float2 pb = __ldg(knb + j), qb = __ldg(knb + s.n_radial + j);
         const int l = s.rad_l[j];
         const int o = s.orb_base[j];
-        float ua = (ca.x + ta * (ca.y + ta * (ca.z + ta * ca.w))) * ma;
-        float ub = (cb.x + tb * (cb.y + tb * (cb.z + tb * cb.w))) * mb;
+        float ua = (pa.x * a00 + qa.x * a01 + pa.y * a10 + qa.y * a11) * ma;
+        float ub = (pb.x * b00 + qb.x * b01 + pb.y * b10 + qb.y * b11) * mb;
         if (tinya) ua = (l == 0) ? ua : 0.f;  // centre limit: phi = R(0) Y00 for l = 0, 0 otherwise
         if (tinyb) ub = (l == 0) ? ub : 0.f;
         for (int q = 0; q < l; ++q) { ua *= ia; ub *= ib; }

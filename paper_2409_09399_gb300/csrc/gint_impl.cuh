@@ -36,6 +36,7 @@ struct SpeciesDev {
     float rc_f;
     float inv_dr_f;
     int64_t tab_off;
+    int64_t knot_off;  // offset of the species' FP32 knot table in float2 units
     int rad_l[kMaxRadial];
     signed char orb_rad[kMaxNw];  // radial function of each orbital
     signed char orb_l[kMaxNw];
@@ -90,6 +91,7 @@ struct Problem {
     const SpeciesDev* sp;
     const double* coef64;
     const float* coef32;
+    const float2* knot32;        // per knot and radial function (R(r_k), dr R'(r_k)) in FP32
     const ExtAtom* ext;
     const int64_t* brick_start;  // n_bricks + 1
     const int32_t* brick_atoms;  // ext indices, ascending per brick
@@ -101,6 +103,29 @@ struct Problem {
     int n_atoms;
     int n_species;
     int* err;                    // device error flags (bit set)
+};
+
+// One cell of a batched launch: its problem and its call's buffers, and the
+// position of its bricks in the batch's work queue (items [item0, item0 + n_work)).
+struct CellJob {
+    Problem P;
+    const double* V;
+    double* H;
+    const unsigned char* Dt;     // tensor-core copy of D
+    const unsigned char* Dzero;  // a zero tile of it
+    const int* dq;               // exact form: row maxima of D
+    double* rho;
+    double* facc;
+    double* acc_e;
+    int item0;
+    int pad;
+};
+
+// The (cell, brick) queue of a batched launch: item w belongs to cell item_cell[w].
+struct MultiArgs {
+    const CellJob* jobs;
+    const int* item_cell;
+    int n_items;
 };
 
 // Device error bits.
@@ -136,6 +161,7 @@ struct gint_handle {
     gint::SpeciesDev* d_sp = nullptr;
     double* d_coef64 = nullptr;
     float* d_coef32 = nullptr;
+    float2* d_knot32 = nullptr;
     gint::ExtAtom* d_ext = nullptr;
     int32_t* d_blocks = nullptr;
     int64_t* d_offsets = nullptr;
@@ -164,6 +190,7 @@ struct gint_handle {
         p.sp = d_sp;
         p.coef64 = d_coef64;
         p.coef32 = d_coef32;
+        p.knot32 = d_knot32;
         p.ext = d_ext;
         p.brick_start = d_brick_start;
         p.brick_atoms = d_brick_atoms;

@@ -508,6 +508,7 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
     // ---- species tables
     std::vector<SpeciesDev> spd(n_species);
     std::vector<double> coef;
+    std::vector<float2> knots;  // FP32 knot table: per species, per knot, per radial function
     std::vector<double> rc_sp(n_species);
     std::vector<int> nw_sp(n_species);
     int max_nw = 0;
@@ -524,6 +525,12 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
         D.inv_dr_f = (float)(1.0 / r0.dr);
         D.n_int = r0.n_knots - 1;
         D.tab_off = (int64_t)coef.size();
+        D.knot_off = (int64_t)knots.size();
+        for (int k = 0; k < r0.n_knots; ++k)
+            for (int j = 0; j < S.n_radial; ++j) {
+                const gint_radial& R = S.radial[j];
+                knots.push_back(make_float2((float)R.y[k], (float)(R.dr * R.dy[k])));
+            }
         int lmax = 0, norb = 0;
         for (int j = 0; j < S.n_radial; ++j) {
             D.rad_l[j] = S.radial[j].l;
@@ -581,6 +588,7 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
     GINT_TRY(dev_upload(&h->d_sp, spd.data(), spd.size()));
     GINT_TRY(dev_upload(&h->d_coef64, coef.data(), coef.size()));
     GINT_TRY(dev_upload(&h->d_coef32, coef32.data(), coef32.size()));
+    GINT_TRY(dev_upload(&h->d_knot32, knots.data(), knots.size()));
 
     // ---- cell and grid
     CellDev c;
@@ -798,7 +806,7 @@ static void free_handle(gint_handle* h) {
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(h->device);
-    void* ptrs[] = {h->d_sp, h->d_coef64, h->d_coef32, h->d_ext, h->d_blocks, h->d_offsets, h->d_row_start,
+    void* ptrs[] = {h->d_sp, h->d_coef64, h->d_coef32, h->d_knot32, h->d_ext, h->d_blocks, h->d_offsets, h->d_row_start,
                     h->d_mirror, h->d_brick_start, h->d_brick_atoms, h->d_work, h->d_empty, h->d_err, h->d_red,
                     h->d_scratch, h->d_nw_atom, h->d_atom_sp, h->d_facc, h->d_dt, h->d_dq, h->d_zero};
     for (void* p : ptrs)

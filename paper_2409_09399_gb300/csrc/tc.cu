@@ -33,6 +33,7 @@
 // The atom-to-brick displacement is taken in FP64 once per (brick, atom) and
 // split into two FP32 words; in-brick offsets are FP32.
 #include <algorithm>
+#include <cstring>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -151,16 +152,36 @@ __device__ __forceinline__ void fix_split3(float s, unsigned short& n16, unsigne
 }
 __device__ __forceinline__ float exp2i(int e) { return __int_as_float((127 + e) << 23); }  // 2^e, |e| < 127
 
-template <typename H16, bool kExact>
-__global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const double* V, double* H) {
+// kMulti: the work queue spans the bricks of many cells (a batch, MultiArgs);
+// the problem, V and H of an item come from its cell's CellJob.
+template <typename H16, bool kExact, bool kMulti>
+__global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_constant__ TcArgs A, const double* V_in, double* H_in,
+                                                                const __grid_constant__ MultiArgs M) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem<kExact>& S = *reinterpret_cast<TcSmem<kExact>*>(smem_raw);
     using C = TcCfg<kExact>;
     constexpr int kPassCols = C::kPassCols;
     constexpr int kAP = C::kAPieceBytes, kBP = C::kBPieceBytes, kBOff = C::kBOff;
-    const Problem& P = A.P;
-    const GridDev& g = P.g;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const Problem* Pc = &A.P;  // problem, V and H of the current item
+    const double* Vc = V_in;
+    double* Hc = H_in;
+    int cur_cell = -1;
+    // per-cell tables: species (shared memory copy) and the in-brick point offsets (the same
+    // for every brick of a cell): FP64, rounded once to FP32
+    auto cell_setup = [&](const Problem& Q) {
+        if (tid < Q.n_species) species_fast_from(Q.sp[tid], S.spf[tid]);
+        const GridDev& gq = Q.g;
+        for (int p = tid; p < gq.bpad && p < C::kPts; p += kTcThreads) {
+            const int l2 = p % gq.B[2], l1 = (p / gq.B[2]) % gq.B[1], l0 = p / (gq.B[2] * gq.B[1]);
+            float4 q4;
+            q4.x = (float)(l0 * gq.step[0][0] + l1 * gq.step[1][0] + l2 * gq.step[2][0]);
+            q4.y = (float)(l0 * gq.step[0][1] + l1 * gq.step[1][1] + l2 * gq.step[2][1]);
+            q4.z = (float)(l0 * gq.step[0][2] + l1 * gq.step[1][2] + l2 * gq.step[2][2]);
+            q4.w = 0.f;
+            S.pt[p] = q4;
+        }
+    };
 
     if (warp == 0) {
         tc::tmem_alloc(&S.tmem, 512);
@@ -175,17 +196,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         S.abort = 0;
     }
-    if (tid < P.n_species) species_fast_from(P.sp[tid], S.spf[tid]);
-    // in-brick point offsets (the same for every brick): FP64, rounded once to FP32
-    for (int p = tid; p < g.bpad && p < C::kPts; p += kTcThreads) {
-        const int l2 = p % g.B[2], l1 = (p / g.B[2]) % g.B[1], l0 = p / (g.B[2] * g.B[1]);
-        float4 q4;
-        q4.x = (float)(l0 * g.step[0][0] + l1 * g.step[1][0] + l2 * g.step[2][0]);
-        q4.y = (float)(l0 * g.step[0][1] + l1 * g.step[1][1] + l2 * g.step[2][1]);
-        q4.z = (float)(l0 * g.step[0][2] + l1 * g.step[1][2] + l2 * g.step[2][2]);
-        q4.w = 0.f;
-        S.pt[p] = q4;
-    }
+    if (!kMulti) cell_setup(A.P);
     for (int r = tid; r < C::kRows; r += kTcThreads) S.rowtab[r] = (unsigned short)((((r >> 3) * (kTcChunk / 8)) << 7) + ((r & 7) << 4));
     tc::fence_before_sync();
     __syncthreads();
@@ -194,7 +205,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
     // completed phases of each barrier (every thread that waits on a barrier keeps its count)
     uint32_t uses[2] = {0, 0};  // chunks produced into / issued from buffer b
     uint32_t dones = 0;
-    const float4* coef4 = reinterpret_cast<const float4*>(P.coef32);
     const bool issuer_warp = warp == kTcProdThreads / 32;
     const int half = warp >> 3;  // producer half (0 or 1) for warps 0-15
     const int lt = tid & (kTcHalf - 1);
@@ -203,8 +213,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
         if (tid == 0) S.work = atomicAdd(A.counter, 1);
         __syncthreads();
         const int w = S.work;
-        if (w >= P.n_work || S.abort) break;
-        const int brick = P.work[w];
+        if (w >= (kMulti ? M.n_items : A.P.n_work) || S.abort) break;
+        int wl = w;
+        if (kMulti) {
+            const int c = M.item_cell[w];
+            const CellJob& J = M.jobs[c];
+            wl = w - J.item0;
+            if (c != cur_cell) {  // uniform: every thread read the same item
+                cur_cell = c;
+                Pc = &J.P;
+                Vc = J.V;
+                Hc = J.H;
+                cell_setup(J.P);
+                __syncthreads();
+            }
+        }
+        const Problem& P = *Pc;
+        const GridDev& g = P.g;
+        const double* V = Vc;
+        double* H = Hc;
+        const float2* knot2 = P.knot32;
+        const int brick = P.work[wl];
         int b0, b1, b2;
         brick_coords(g, brick, b0, b1, b2);
         const int64_t s0 = P.brick_start[brick];
@@ -405,7 +434,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
                                 stB(0, bh0, bh1); stB(1, bl0, bl1);
                             }
                         };
-                        if (!orbitals_fast2<!kExact>(sf, coef4, ax, ay, az, bx, by, bz, put2))
+                        if (!orbitals_fast2<!kExact>(sf, knot2, ax, ay, az, bx, by, bz, put2))
                             for (int o = 0; o < X.nw; ++o) {
                                 const int r = rbase + o;
                                 const int offB = kBOff + S.rowtab[r] + qoff;
@@ -545,7 +574,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(TcArgs A, const dou
     __syncthreads();
     if (issuer_warp && lane == 0) tc::mma_commit(&S.done);
     (void)tc::mbar_wait(&S.done, dones & 1, kWaitLimit);
-    if (S.abort && tid == 0) atomicOr(P.err, kErrTimeout);
+    if (S.abort && tid == 0) atomicOr(Pc->err, kErrTimeout);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
@@ -600,9 +629,9 @@ gint_status tc_vlocal(gint_handle* h, int form, const double* V, double* H, int 
     const size_t smem = exact ? tc_smem_bytes<true>() : tc_smem_bytes<false>();
 #define GINT_LAUNCH_VL(H16, X)                                                                                 \
     do {                                                                                                       \
-        GINT_CUDA_TRY(cudaFuncSetAttribute(k_vlocal_tc<H16, X>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+        GINT_CUDA_TRY(cudaFuncSetAttribute(k_vlocal_tc<H16, X, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                            (int)smem));                                                        \
-        k_vlocal_tc<H16, X><<<h->sm_count, kTcThreads, smem, st>>>(A, V, H);                                   \
+        k_vlocal_tc<H16, X, false><<<h->sm_count, kTcThreads, smem, st>>>(A, V, H, MultiArgs{});              \
     } while (0)
     if (form == 1) GINT_LAUNCH_VL(__nv_bfloat16, false);
     else if (form == 2) GINT_LAUNCH_VL(__half, true);
@@ -613,6 +642,39 @@ gint_status tc_vlocal(gint_handle* h, int form, const double* V, double* H, int 
         k_norm_h<<<(unsigned)((h->n_blocks * 32 + 255) / 256), 256, 0, st>>>(A.P, h->d_atom_sp, h->n_blocks, H);
         GINT_CUDA_TRY(cudaGetLastError());
     }
+    return GINT_OK;
+}
+
+// Exact form, H not accumulated into: the FP64 harmonic normalisation of a cell's H.
+gint_status launch_norm_h(gint_handle* h, double* H, cudaStream_t st) {
+    if (h->n_blocks == 0) return GINT_OK;
+    k_norm_h<<<(unsigned)((h->n_blocks * 32 + 255) / 256), 256, 0, st>>>(h->problem(), h->d_atom_sp, h->n_blocks, H);
+    GINT_CUDA_TRY(cudaGetLastError());
+    return GINT_OK;
+}
+
+// One launch over the (cell, brick) queue of a batch: every cell's H (zeroed by the
+// caller; the exact form leaves the normalisation to launch_norm_h).  The cells must
+// pass tc_vlocal_check for `form`.
+gint_status tc_vlocal_multi(int form, const MultiArgs& M, int* counter, int sm_count, cudaStream_t st) {
+    if (M.n_items == 0) return GINT_OK;
+    TcArgs A;
+    memset(&A, 0, sizeof(A));
+    A.counter = counter;
+    A.norm_after = form == 2 ? 1 : 0;
+    GINT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
+    const size_t smem = form == 2 ? tc_smem_bytes<true>() : tc_smem_bytes<false>();
+#define GINT_LAUNCH_VLM(H16, X)                                                                                \
+    do {                                                                                                       \
+        GINT_CUDA_TRY(cudaFuncSetAttribute(k_vlocal_tc<H16, X, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                           (int)smem));                                                        \
+        k_vlocal_tc<H16, X, true><<<sm_count, kTcThreads, smem, st>>>(A, nullptr, nullptr, M);                 \
+    } while (0)
+    if (form == 1) GINT_LAUNCH_VLM(__nv_bfloat16, false);
+    else if (form == 2) GINT_LAUNCH_VLM(__half, true);
+    else GINT_LAUNCH_VLM(__half, false);
+#undef GINT_LAUNCH_VLM
+    GINT_CUDA_TRY(cudaGetLastError());
     return GINT_OK;
 }
 

@@ -28,6 +28,7 @@
 //     forms rho_p = sum phi G, or F_I += 2 W_p grad phi . G with the virial
 //     and the energy, reduced per image in shared memory before FP64 atomics.
 #include <algorithm>
+#include <cstring>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -223,17 +224,18 @@ __global__ void k_format_d(Problem P, const int32_t* mirror, const int* nw_atom,
     }
 }
 
-template <typename H16, bool kForce, bool kExact>
-__global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* counter, const double* V,
-                                                            const unsigned char* Dt, const unsigned char* Dzero,
-                                                            const int* dq, double* rho, double* facc, double* acc_e) {
+// kMulti: the work queue spans the bricks of many cells (a batch, MultiArgs); the
+// problem and the buffers of an item come from its cell's CellJob.
+template <typename H16, bool kForce, bool kExact, bool kMulti>
+__global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_constant__ CellJob J_in, int* counter, const __grid_constant__ MultiArgs M) {
     constexpr int kCols = kExact ? kMaxCols / 2 : kMaxCols;  // output columns of one column group
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem<kExact>& S = *reinterpret_cast<Smem<kExact>*>(smem_raw);
     using C = RfCfg<kExact>;
     constexpr int kBPiece = C::kBPiece;
-    const GridDev& g = P.g;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const CellJob* Jc = &J_in;  // problem and buffers of the current item
+    int cur_cell = -1;
 
     if (warp == 0) {
         tc::tmem_alloc(&S.tmem, kMaxCols);
@@ -249,29 +251,54 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         S.abort = 0;
     }
-    if (tid < P.n_species) species_fast_from(P.sp[tid], S.spf[tid]);
+    if (!kMulti && tid < J_in.P.n_species) species_fast_from(J_in.P.sp[tid], S.spf[tid]);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = S.tmem;
-    // exact form: one quantum 2^qa for every orbital value (the largest per-orbital quantum)
-    int qa = -126;
-    if (kExact)
-        for (int sp = 0; sp < P.n_species; ++sp)
+    // exact form: one quantum 2^qa for every orbital value (the largest per-orbital quantum of the cell)
+    float qa_inv = 1.f, qa_f = 1.f;
+    auto set_qa = [&](const Problem& Q) {
+        int qa = -126;
+        for (int sp = 0; sp < Q.n_species; ++sp)
             for (int o = 0; o < S.spf[sp].nw; ++o) qa = max(qa, (int)S.spf[sp].qe[o]);
-    const float qa_inv = kExact ? exp2f_i(-qa) : 1.f, qa_f = kExact ? exp2f_i(qa) : 1.f;
+        qa_inv = exp2f_i(-qa);
+        qa_f = exp2f_i(qa);
+    };
+    if (kExact && !kMulti) set_qa(J_in.P);
     uint32_t uses[2] = {0, 0};  // steps that used buffer b (every thread counts them)
     uint32_t dones = 0;         // completed phases of done
     uint32_t bissue[2] = {0, 0}, bdone[2] = {0, 0};  // warp 8 lane 0: bulk-copy phases started / waited
     uint32_t chunk = 0;  // global chunk counter (buffer parity)
-    const float4* coef4 = reinterpret_cast<const float4*>(P.coef32);
 
     for (;;) {
         if (tid == 0) S.work = atomicAdd(counter, 1);
         __syncthreads();
         const int w = S.work;
-        if (w >= P.n_work || S.abort) break;
-        const int brick = P.work[w];
+        if (w >= (kMulti ? M.n_items : J_in.P.n_work) || S.abort) break;
+        int wl = w;
+        if (kMulti) {
+            const int c = M.item_cell[w];
+            wl = w - M.jobs[c].item0;
+            if (c != cur_cell) {  // uniform: every thread read the same item
+                cur_cell = c;
+                Jc = &M.jobs[c];
+                if (tid < Jc->P.n_species) species_fast_from(Jc->P.sp[tid], S.spf[tid]);
+                __syncthreads();
+                if (kExact) set_qa(Jc->P);
+            }
+        }
+        const Problem& P = Jc->P;
+        const GridDev& g = P.g;
+        const double* V = Jc->V;
+        const unsigned char* Dt = Jc->Dt;
+        const unsigned char* Dzero = Jc->Dzero;
+        const int* dq = Jc->dq;
+        double* rho = Jc->rho;
+        double* facc = Jc->facc;
+        double* acc_e = Jc->acc_e;
+        const float2* knot2 = P.knot32;
+        const int brick = P.work[wl];
         int b0, b1, b2;
         brick_coords(g, brick, b0, b1, b2);
         const int64_t s0 = P.brick_start[brick];
@@ -403,7 +430,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
                                 *reinterpret_cast<unsigned short*>(A0 + kAPiece + amn(pl, o)) = lo;
                                 if (kExact) *reinterpret_cast<unsigned short*>(A0 + 2 * kAPiece + amn(pl, o)) = l2;
                             };
-                            inside = orbitals_fast<false>(S.spf[X.sp], coef4, dx, dy, dz, put);
+                            inside = orbitals_fast<false>(S.spf[X.sp], knot2, dx, dy, dz, put);
                         }
                         if (!inside)
                             for (int o = 0; o < X.nw; ++o)
@@ -533,7 +560,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
                             e_j += v * gv;
                             if (kForce) { f0 += gx * gv; f1 += gy * gv; f2 += gz * gv; }
                         };
-                        (void)orbitals_fast<kForce>(S.spf[Y.sp], coef4, dx, dy, dz, put);
+                        (void)orbitals_fast<kForce>(S.spf[Y.sp], knot2, dx, dy, dz, put);
                     }
                     rho_p += e_j;
                     if (kForce) {
@@ -588,7 +615,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(Problem P, int* cou
         for (int b = 0; b < 2; ++b)
             if (bissue[b] > bdone[b]) (void)tc::mbar_wait(&S.bfull[b], bdone[b] & 1, kWait);
     }
-    if (S.abort && tid == 0) atomicOr(P.err, kErrTimeout);
+    if (S.abort && tid == 0) atomicOr(Jc->P.err, kErrTimeout);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, kMaxCols);
@@ -629,49 +656,88 @@ gint_status tc_rhoforce_check(const gint_handle* h) {
     return GINT_OK;
 }
 
+// The per-call tensor-core copy of D (and, exact form, its row maxima).
+gint_status tc_format_d(gint_handle* h, int form, const double* D, cudaStream_t st) {
+    gint_status s = ensure_dt(h);
+    if (s != GINT_OK) return s;
+    if (h->n_blocks == 0) return GINT_OK;
+    const Problem P = h->problem();
+    const unsigned grid = (unsigned)((h->n_blocks * 32 + 255) / 256);
+    unsigned char* dt = (unsigned char*)h->d_dt;
+    if (form == 2) {
+        GINT_CUDA_TRY(cudaMemsetAsync(h->d_dq, 0, sizeof(int) * 16 * (size_t)h->n_atoms, st));
+        k_dmax<<<grid, 256, 0, st>>>(P, h->d_mirror, h->d_nw_atom, h->n_blocks, D, h->d_dq);
+        k_format_d<__half, true><<<grid, 256, 0, st>>>(P, h->d_mirror, h->d_nw_atom, h->n_blocks, D, h->d_dq, dt);
+    } else if (form == 1) {
+        k_format_d<__nv_bfloat16, false><<<grid, 256, 0, st>>>(P, h->d_mirror, h->d_nw_atom, h->n_blocks, D, h->d_dq, dt);
+    } else {
+        k_format_d<__half, false><<<grid, 256, 0, st>>>(P, h->d_mirror, h->d_nw_atom, h->n_blocks, D, h->d_dq, dt);
+    }
+    GINT_CUDA_TRY(cudaGetLastError());
+    return GINT_OK;
+}
+
+// A cell's job for the rho/force kernel (D already formatted by tc_format_d).
+CellJob tc_cell_job(gint_handle* h, const double* V, double* H, double* rho, double* facc, double* acc_e) {
+    CellJob J;
+    memset(&J, 0, sizeof(J));
+    J.P = h->problem();
+    J.V = V;
+    J.H = H;
+    J.Dt = (const unsigned char*)h->d_dt;
+    J.Dzero = (const unsigned char*)h->d_zero;
+    J.dq = h->d_dq;
+    J.rho = rho;
+    J.facc = facc;
+    J.acc_e = acc_e;
+    return J;
+}
+
+// One launch of the rho or force kernel: one cell (M.n_items == 0: J) or a batch queue (M).
+static gint_status launch_rf(int form, bool force, const CellJob& J, const MultiArgs& M, bool multi, int* counter,
+                             int sm_count, cudaStream_t st) {
+    const bool exact = form == 2;
+    GINT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
+    const size_t smem = (exact ? sizeof(Smem<true>) : sizeof(Smem<false>)) + 1024;
+#define GINT_LAUNCH_RF(H16, F, X, MU)                                                                          \
+    do {                                                                                                        \
+        GINT_CUDA_TRY(cudaFuncSetAttribute(k_rhoforce_tc<H16, F, X, MU>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                           (int)smem));                                                         \
+        k_rhoforce_tc<H16, F, X, MU><<<sm_count, kThreads, smem, st>>>(J, counter, M);                           \
+    } while (0)
+#define GINT_LAUNCH_RF2(H16, X, MU) \
+    do { if (force) GINT_LAUNCH_RF(H16, true, X, MU); else GINT_LAUNCH_RF(H16, false, X, MU); } while (0)
+    if (multi) {
+        if (form == 1) GINT_LAUNCH_RF2(__nv_bfloat16, false, true);
+        else if (exact) GINT_LAUNCH_RF2(__half, true, true);
+        else GINT_LAUNCH_RF2(__half, false, true);
+    } else {
+        if (form == 1) GINT_LAUNCH_RF2(__nv_bfloat16, false, false);
+        else if (exact) GINT_LAUNCH_RF2(__half, true, false);
+        else GINT_LAUNCH_RF2(__half, false, false);
+    }
+#undef GINT_LAUNCH_RF2
+#undef GINT_LAUNCH_RF
+    GINT_CUDA_TRY(cudaGetLastError());
+    return GINT_OK;
+}
+
 gint_status tc_rhoforce(gint_handle* h, int form, bool force, const double* V, const double* D, double* rho,
                         double* facc, double* acc_e, cudaStream_t st) {
     gint_status s = tc_rhoforce_check(h);
     if (s != GINT_OK) return s;
-    s = ensure_dt(h);
-    if (s != GINT_OK) return s;
-    Problem P = h->problem();
-    const bool exact = form == 2;
-    if (h->n_blocks > 0) {
-        const unsigned grid = (unsigned)((h->n_blocks * 32 + 255) / 256);
-        unsigned char* dt = (unsigned char*)h->d_dt;
-        if (exact) {
-            GINT_CUDA_TRY(cudaMemsetAsync(h->d_dq, 0, sizeof(int) * 16 * (size_t)h->n_atoms, st));
-            k_dmax<<<grid, 256, 0, st>>>(P, h->d_mirror, h->d_nw_atom, h->n_blocks, D, h->d_dq);
-            k_format_d<__half, true><<<grid, 256, 0, st>>>(P, h->d_mirror, h->d_nw_atom, h->n_blocks, D, h->d_dq, dt);
-        } else if (form == 1) {
-            k_format_d<__nv_bfloat16, false><<<grid, 256, 0, st>>>(P, h->d_mirror, h->d_nw_atom, h->n_blocks, D, h->d_dq, dt);
-        } else {
-            k_format_d<__half, false><<<grid, 256, 0, st>>>(P, h->d_mirror, h->d_nw_atom, h->n_blocks, D, h->d_dq, dt);
-        }
-        GINT_CUDA_TRY(cudaGetLastError());
-    }
-    if (h->n_work == 0) return GINT_OK;
-    int* counter = h->d_err + 2;
-    GINT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
-    const size_t smem = (exact ? sizeof(Smem<true>) : sizeof(Smem<false>)) + 1024;
-    const unsigned char* Dt = (const unsigned char*)h->d_dt;
-#define GINT_LAUNCH_RF(H16, F, X)                                                                              \
-    do {                                                                                                        \
-        GINT_CUDA_TRY(cudaFuncSetAttribute(k_rhoforce_tc<H16, F, X>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                           (int)smem));                                                         \
-        k_rhoforce_tc<H16, F, X><<<h->sm_count, kThreads, smem, st>>>(P, counter, V, Dt, (const unsigned char*)h->d_zero, h->d_dq, rho, facc, acc_e); \
-    } while (0)
-    if (form == 1) {
-        if (force) GINT_LAUNCH_RF(__nv_bfloat16, true, false); else GINT_LAUNCH_RF(__nv_bfloat16, false, false);
-    } else if (exact) {
-        if (force) GINT_LAUNCH_RF(__half, true, true); else GINT_LAUNCH_RF(__half, false, true);
-    } else {
-        if (force) GINT_LAUNCH_RF(__half, true, false); else GINT_LAUNCH_RF(__half, false, false);
-    }
-#undef GINT_LAUNCH_RF
-    GINT_CUDA_TRY(cudaGetLastError());
-    return GINT_OK;
+    s = tc_format_d(h, form, D, st);
+    if (s != GINT_OK || h->n_work == 0) return s;
+    return launch_rf(form, force, tc_cell_job(h, V, nullptr, rho, facc, acc_e), MultiArgs{}, false, h->d_err + 2,
+                     h->sm_count, st);
+}
+
+// One launch over the (cell, brick) queue of a batch (every cell's D formatted, cells checked).
+gint_status tc_rhoforce_multi(int form, bool force, const MultiArgs& M, int* counter, int sm_count, cudaStream_t st) {
+    if (M.n_items == 0) return GINT_OK;
+    CellJob none;
+    memset(&none, 0, sizeof(none));
+    return launch_rf(form, force, none, M, true, counter, sm_count, st);
 }
 
 }  // namespace gint
