@@ -46,6 +46,25 @@ def test_batch_mixed_vs_single_and_fp64(cuda):
     H, rho, F, sig, E = _run_batch(b, systems, Vs, Ds)
     # a second launch with new output buffers re-captures; with the same ones it replays
     H2, rho2, F2, sig2, E2 = _run_batch(b, systems, Vs, Ds)
+    # time the graph (replays) against the same calls made one cell at a time
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(3):
+        b.run(Vs, Ds, H2, rho2, F2, sig2, E2)
+    e.record()
+    torch.cuda.synchronize()
+    t_graph = a.elapsed_time(e) / 3
+    a.record()
+    for _ in range(3):
+        for i, h in enumerate(b.handles):
+            h.vlocal(Vs[i], H2[i])
+            h.rho(Ds[i], rho2[i])
+            h.force_stress(Vs[i], Ds[i], out=(F2[i], sig2[i], torch.empty((h.n_atoms, 3, 3), dtype=torch.float64,
+                                                                          device="cuda"), E2[i]))
+    e.record()
+    torch.cuda.synchronize()
+    t_cells = a.elapsed_time(e) / 3
+    print(f"batch of {len(systems)} cells: one graph launch {t_graph:.2f} ms, cell by cell {t_cells:.2f} ms")
     worst = {"H": 0.0, "rho": 0.0, "F": 0.0}
     for i, (s, h) in enumerate(zip(systems, b.handles)):
         # same kernels one cell at a time: equal up to the order of FP64 atomics
