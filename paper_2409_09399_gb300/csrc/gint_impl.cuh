@@ -96,6 +96,8 @@ struct Problem {
     const int64_t* brick_start;  // n_bricks + 1
     const int32_t* brick_atoms;  // ext indices, ascending per brick
     const int32_t* work;         // non-empty brick ids, natural order
+    const int64_t* pair_start;   // n_bricks + 1: first entry of each brick's pair table
+    const int32_t* pairs;        // per brick, na x na: block (I_a, I_b, t_b - t_a) of images a, b, -1 if none
     int n_work;
     const int32_t* blocks;       // n_blocks x 5
     const int64_t* offsets;      // n_blocks + 1
@@ -170,6 +172,8 @@ struct gint_handle {
     int64_t* d_brick_start = nullptr;
     int32_t* d_brick_atoms = nullptr;
     int32_t* d_work = nullptr;        // non-empty bricks
+    int64_t* d_pair_start = nullptr;  // per-brick pair tables (see Problem::pairs)
+    int32_t* d_pairs = nullptr;
     int32_t* d_empty = nullptr;       // empty bricks
     int* d_err = nullptr;             // [0] device check flags, [2] work counter
     int* d_nw_atom = nullptr;         // orbitals of every atom
@@ -195,6 +199,8 @@ struct gint_handle {
         p.brick_start = d_brick_start;
         p.brick_atoms = d_brick_atoms;
         p.work = d_work;
+        p.pair_start = d_pair_start;
+        p.pairs = d_pairs;
         p.n_work = (int)n_work;
         p.blocks = d_blocks;
         p.offsets = d_offsets;

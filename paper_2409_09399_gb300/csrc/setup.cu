@@ -395,6 +395,38 @@ __global__ void k_sort_bricks(int64_t n_bricks, const int64_t* start, int32_t* a
 }
 
 // Per-brick statistics: orbital count, pattern pairs; work-list flags.
+// Pair tables of the bricks (once per geometry): for images a, b of a brick
+// (brick-local order), the block (I_a, I_b, t_b - t_a) when |R_b - R_a| <
+// rc_a + rc_b (FP64, as the pattern), else -1.  One warp per brick.
+__global__ void k_pair_count(int64_t n_bricks, const int64_t* brick_start, int64_t* cnt) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_bricks) return;
+    const int64_t na = brick_start[b + 1] - brick_start[b];
+    cnt[b] = na * na;
+}
+
+__global__ void k_brick_pairs(Problem P, int64_t n_bricks, const double* rc_sp, int32_t* pairs) {
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= n_bricks) return;
+    const int64_t s0 = P.brick_start[b];
+    const int na = (int)(P.brick_start[b + 1] - s0);
+    const int64_t ps = P.pair_start[b];
+    for (int q = lane; q < na * na; q += 32) {
+        const int a1 = q / na, a2 = q - a1 * na;
+        const ExtAtom& X = P.ext[P.brick_atoms[s0 + a1]];
+        const ExtAtom& Y = P.ext[P.brick_atoms[s0 + a2]];
+        const double dx = Y.p[0] - X.p[0], dy = Y.p[1] - X.p[1], dz = Y.p[2] - X.p[2];
+        const double cut = rc_sp[X.species] + rc_sp[Y.species];
+        int64_t blk = -1;
+        if (dx * dx + dy * dy + dz * dz < cut * cut) {
+            blk = find_block(P, X.atom, Y.atom, Y.t[0] - X.t[0], Y.t[1] - X.t[1], Y.t[2] - X.t[2]);
+            if (blk < 0) atomicOr(P.err, kErrPatternMissing);
+        }
+        pairs[ps + q] = (int32_t)blk;
+    }
+}
+
 __global__ void k_brick_stats(Problem P, int64_t n_bricks, const double* rc_sp, int64_t* nonempty_flag,
                               int64_t* pairs, int* max_atoms, int* max_orb) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -772,6 +804,22 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
         k_sum_i64<<<(unsigned)((nbk + 255) / 256), 256, 0, st>>>(d_pairs, nbk, d_sum);
         GINT_CUDA_TRY(cudaGetLastError());
     }
+    // ---- per-brick pair tables
+    {
+        int64_t* d_pcnt = nullptr;
+        GINT_CUDA_TRY(cudaMalloc(&d_pcnt, sizeof(int64_t) * (nbk + 1)));
+        tmp.p.push_back(d_pcnt);
+        k_pair_count<<<(unsigned)((nbk + 255) / 256), 256, 0, st>>>(nbk, h->d_brick_start, d_pcnt);
+        GINT_CUDA_TRY(cudaGetLastError());
+        GINT_CUDA_TRY(cudaMalloc(&h->d_pair_start, sizeof(int64_t) * (nbk + 1)));
+        GINT_TRY(scan_exclusive(d_pcnt, nbk, h->d_pair_start, st));
+        int64_t n_pair_entries = 0;
+        GINT_CUDA_TRY(cudaMemcpy(&n_pair_entries, h->d_pair_start + nbk, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        GINT_CUDA_TRY(cudaMalloc(&h->d_pairs, sizeof(int32_t) * std::max<int64_t>(1, n_pair_entries)));
+        Problem P = h->problem();
+        k_brick_pairs<<<(unsigned)((nbk * 32 + 255) / 256), 256, 0, st>>>(P, nbk, d_rc, h->d_pairs);
+        GINT_CUDA_TRY(cudaGetLastError());
+    }
     GINT_TRY(scan_exclusive(d_flag, nbk, d_pos_ne, st));
     GINT_CUDA_TRY(cudaMemcpy(&h->n_work, d_pos_ne + nbk, sizeof(int64_t), cudaMemcpyDeviceToHost));
     h->n_empty = nbk - h->n_work;
@@ -807,7 +855,7 @@ static void free_handle(gint_handle* h) {
     cudaGetDevice(&prev);
     cudaSetDevice(h->device);
     void* ptrs[] = {h->d_sp, h->d_coef64, h->d_coef32, h->d_knot32, h->d_ext, h->d_blocks, h->d_offsets, h->d_row_start,
-                    h->d_mirror, h->d_brick_start, h->d_brick_atoms, h->d_work, h->d_empty, h->d_err, h->d_red,
+                    h->d_mirror, h->d_brick_start, h->d_brick_atoms, h->d_work, h->d_pair_start, h->d_pairs, h->d_empty, h->d_err, h->d_red,
                     h->d_scratch, h->d_nw_atom, h->d_atom_sp, h->d_facc, h->d_dt, h->d_dq, h->d_zero};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -96,6 +96,7 @@ template <bool kExact> struct TcSmem {
     unsigned char row_mu[C::kRows];
     unsigned short rowtab[C::kRows];  // byte offset of row r's 16-byte segment in a piece
     double row_s[C::kRows];           // exact form: [ylm_norm x] 2^qeu of row r (FP64)
+    float row_f[C::kRows];            // exact form: 2^qeu of row r
     unsigned char seg_tile[kTcMaxSeg];  // segment: row tile, columns [c0, c1), TMEM column
     short seg_c0[kTcMaxSeg], seg_c1[kTcMaxSeg], seg_tcol[kTcMaxSeg];
     int pass_first[kTcMaxSeg + 1];      // first segment of each pass
@@ -151,6 +152,16 @@ __device__ __forceinline__ void fix_split3(float s, unsigned short& n16, unsigne
     l2 = __half_as_ushort(__float2half_rn(r - __half2float(h1)));
 }
 __device__ __forceinline__ float exp2i(int e) { return __int_as_float((127 + e) << 23); }  // 2^e, |e| < 127
+
+// Exact FP32 -> FP64 widening with integer operations (sign, exponent rebias by
+// 1023 - 127 = 896, mantissa shifted into place); zero and FP32 subnormals give 0.
+__device__ __forceinline__ double f2d_exact(float x) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
 
 // kMulti: the work queue spans the bricks of many cells (a batch, MultiArgs);
 // the problem, V and H of an item come from its cell's CellJob.
@@ -282,8 +293,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                 for (int o = 0; o < S.at[i].nw; ++o) {
                     S.row_atom[off + o] = (unsigned char)i;
                     S.row_mu[off + o] = (unsigned char)o;
-                    if (kExact)
+                    if (kExact) {
                         S.row_s[off + o] = (A.norm_after ? 1.0 : ylm_norm(sd.orb_l[o], sd.orb_m[o])) * (double)exp2i(sf.qeu[o]);
+                        S.row_f[off + o] = exp2i(sf.qeu[o]);
+                    }
                 }
                 off += S.at[i].nw;
             }
@@ -316,24 +329,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
         const float wscale = 1.f / S.scale_inv;
         for (int p = tid; p < g.bpad; p += kTcThreads) S.pt[p].w *= wscale;
         const int nrow = S.nrow, npass = S.npass;
-        // pair table: offsets of canonical blocks for pairs within cutoff
-        for (int q = tid; q < na * na; q += kTcThreads) {
-            const int a1 = q / na, a2 = q - a1 * na;
-            if (a1 > a2) continue;
-            int off = -1;
-            const TcAtom &X = S.at[a1], &Y = S.at[a2];
-            // FP32 distance with a margin: only pairs within rc1 + rc2 are looked up
-            const float dx = (Y.c_hi[0] - X.c_hi[0]) + (Y.c_lo[0] - X.c_lo[0]);
-            const float dy = (Y.c_hi[1] - X.c_hi[1]) + (Y.c_lo[1] - X.c_lo[1]);
-            const float dz = (Y.c_hi[2] - X.c_hi[2]) + (Y.c_lo[2] - X.c_lo[2]);
-            const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
-            const float cut = P.sp[X.sp].rc_f + P.sp[Y.sp].rc_f;
-            if (dist < cut + 1e-3f) {
-                const int64_t blk = find_block(P, X.I, Y.I, Y.t[0] - X.t[0], Y.t[1] - X.t[1], Y.t[2] - X.t[2]);
-                if (blk >= 0) off = (int)blk;
-                else if (dist < cut - 1e-3f) atomicOr(P.err, kErrPatternMissing);
+        // pair table of the brick (built once per geometry): block (I_a1, I_a2, t_a2 - t_a1), a1 <= a2
+        {
+            const int32_t* pt = P.pairs + P.pair_start[brick];
+            for (int q = tid; q < na * na; q += kTcThreads) {
+                const int a1 = q / na, a2 = q - a1 * na;
+                if (a1 <= a2) S.pairblk[pair_index(a1, a2)] = __ldg(pt + q);
             }
-            S.pairblk[pair_index(a1, a2)] = off;
         }
         // zero the padding rows [nrow, round128(nrow)) of both chunk buffers (B pieces; A pieces
         // too in the three-product form, where A holds every row)
@@ -519,6 +521,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                     const int mu = rvalid ? S.row_mu[r] : 0;
                     const int ngrp = (S.seg_c1[sg] - cs0) >> 4;
                     const double qr = kExact && rvalid ? S.row_s[r] * (double)sinv : (double)sinv;
+                    const float qrf = kExact && rvalid ? S.row_f[r] * sinv : sinv;  // powers of two
                     for (int gq = warp >> 2; gq < ngrp; gq += 4) {
                         float v[16], v1[16];
                         const uint32_t ta = tmem + ((uint32_t)lane_base << 16) + (uint32_t)(S.seg_tcol[sg] + 16 * gq);
@@ -535,30 +538,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                             if (blk < 0) continue;
                             const int64_t off = __ldg(P.offsets + blk);
                             const int nu = S.row_mu[col];
-                            // three-product form: power-of-two scale (exact); exact form: FP64 row and
-                            // column factors (harmonic normalisation x quantum) and 2^-s
-                            // with norm_after the factors are a power of two p2: the two accumulators are
-                            // added with an error-free FP32 two-sum, scaled exactly, and joined in FP64
-                            double val;
+                            const int nw2 = S.at[a2].nw;
+                            if (a1 == a2 && r > col) continue;  // same image: symmetric block, keep r <= col
+                            auto emit = [&](double x) {
+                                atomicAdd(H + off + mu * nw2 + nu, x);
+                                if (a1 == a2 && mu != nu) atomicAdd(H + off + nu * nw2 + mu, x);
+                            };
+                            // Three-product form: power-of-two scale (exact), widened to FP64 by bit
+                            // arithmetic (no FP64 pipe).  Exact form with norm_after: the factors are a
+                            // power of two p2; the two accumulators are added with an error-free FP32
+                            // two-sum, scaled exactly, and both parts are added to H.  Exact form
+                            // accumulating into H: FP64 row and column factors (normalisation x quantum).
                             if (!kExact) {
-                                val = (double)(v[jj] * sinv);
+                                emit(f2d_exact(v[jj] * sinv));
                             } else if (A.norm_after) {
-                                const float p2 = (float)(qr * S.row_s[col]);
+                                const float p2 = qrf * S.row_f[col];
                                 const float a = v[jj], b = v1[jj];
                                 const float sm = a + b, bb = sm - a;
                                 const float er = (a - (sm - bb)) + (b - bb);
-                                val = (double)(sm * p2) + (double)(er * p2);
+                                emit(f2d_exact(sm * p2));
+                                if (er != 0.f) emit(f2d_exact(er * p2));
                             } else {
-                                val = ((double)v[jj] + (double)v1[jj]) * (qr * S.row_s[col]);
-                            }
-                            const int nw2 = S.at[a2].nw;
-                            if (a1 == a2) {
-                                // same atom image: the block is symmetric; keep r <= col and mirror
-                                if (r > col) continue;
-                                atomicAdd(H + off + mu * nw2 + nu, val);
-                                if (mu != nu) atomicAdd(H + off + nu * nw2 + mu, val);
-                            } else {
-                                atomicAdd(H + off + mu * nw2 + nu, val);
+                                emit(((double)v[jj] + (double)v1[jj]) * (qr * S.row_s[col]));
                             }
                         }
                     }

@@ -329,23 +329,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
             }
         }
         __syncthreads();
-        // ordered pair table: B rows of N image a2 for K image a1 come from block (I_a2, I_a1, T_a1 - T_a2)
-        for (int q = tid; q < na * na; q += kThreads) {
-            const int a1 = q / na, a2 = q - a1 * na;
-            const Atom &X = S.at[a1], &Y = S.at[a2];
-            // FP32 distance with a margin: only pairs within rc1 + rc2 are looked up
-            const float dx = (Y.c_hi[0] - X.c_hi[0]) + (Y.c_lo[0] - X.c_lo[0]);
-            const float dy = (Y.c_hi[1] - X.c_hi[1]) + (Y.c_lo[1] - X.c_lo[1]);
-            const float dz = (Y.c_hi[2] - X.c_hi[2]) + (Y.c_lo[2] - X.c_lo[2]);
-            const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
-            const float cut = P.sp[X.sp].rc_f + P.sp[Y.sp].rc_f;
-            int blk = -1;
-            if (dist < cut + 1e-3f) {
-                const int64_t f = find_block(P, Y.I, X.I, X.t[0] - Y.t[0], X.t[1] - Y.t[1], X.t[2] - Y.t[2]);
-                if (f >= 0) blk = (int)f;
-                else if (dist < cut - 1e-3f) atomicOr(P.err, kErrPatternMissing);
+        // ordered pair table: B rows of N image a2 for K image a1 come from block (I_a2, I_a1, T_a1 - T_a2),
+        // entry (a2, a1) of the brick's pair table (built once per geometry)
+        {
+            const int32_t* pt = P.pairs + P.pair_start[brick];
+            for (int q = tid; q < na * na; q += kThreads) {
+                const int a1 = q / na, a2 = q - a1 * na;
+                S.pairblk[q] = __ldg(pt + a2 * na + a1);
             }
-            S.pairblk[q] = blk;
         }
         __syncthreads();
 
