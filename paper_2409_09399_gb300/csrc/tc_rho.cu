@@ -80,6 +80,7 @@ template <bool kExact> struct Smem {
     float Gst[8][32][17];                // epilogue: G values of one image per lane (padded row)
     float rho_part[128];                 // rho of the tile's points over earlier column groups
     float rho_half[128];                 // partial rho from warps 4-7
+    float qd[kMaxCols];                  // exact form: G scale 2^(qa + qD) of each output column of the group
     SpeciesFast spf[kMaxSpecies];
     unsigned char act[kMaxAtoms];
     unsigned long long active_mask;
@@ -125,6 +126,14 @@ template <> struct Split<__nv_bfloat16> {
 // byte offset of element (row r, k) in a K-major piece with 16 K-columns:
 // core (r/8, k/8) at ((r/8)*2 + k/8)*128, row r%8 at *16, column k%8 at *2
 __device__ __forceinline__ int kmaj16(int r, int k) { return ((((r >> 3) << 1) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1); }
+// Pre-formatted D tile of one block (16 x 16, K-major core matrices): the pieces
+// are interleaved per group of 8 rows, [rows 0-7: piece 0, 1(, 2)][rows 8-15: ...],
+// 256 B per (row group, piece), so a tile is one contiguous copy into its image
+// slot of B and each piece is a K-major operand with row-group stride kP * 256 B.
+__device__ __forceinline__ int dt_off(int i, int j, int pc, int kP) {
+    return ((((i >> 3) * kP + pc)) << 8) + ((j >> 3) << 7) + ((i & 7) << 4) + ((j & 7) << 1);
+}
+
 // byte offset of A element (point p, orbital slot o) in an MN-major A piece
 __device__ __forceinline__ int amn(int p, int o) { return (o >> 3) * kALbo + (p >> 3) * kASbo + ((o & 7) << 4) + ((p & 7) << 1); }
 
@@ -217,10 +226,10 @@ __global__ void k_format_d(Problem P, const int32_t* mirror, const int* nw_atom,
         unsigned short hi, lo, l2 = 0;
         if (kExact) fix_split3(v * exp2f_i(-dq_exp(dq[16 * I + i])), hi, lo, l2);
         else Split<H16>::run(v, hi, lo);
-        const int o = kmaj16(i, j);
-        *reinterpret_cast<unsigned short*>(out + o) = hi;
-        *reinterpret_cast<unsigned short*>(out + kDtPiece + o) = lo;
-        if (kExact) *reinterpret_cast<unsigned short*>(out + 2 * kDtPiece + o) = l2;
+        constexpr int kP = kExact ? 3 : 2;
+        *reinterpret_cast<unsigned short*>(out + dt_off(i, j, 0, kP)) = hi;
+        *reinterpret_cast<unsigned short*>(out + dt_off(i, j, 1, kP)) = lo;
+        if (kExact) *reinterpret_cast<unsigned short*>(out + dt_off(i, j, 2, kP)) = l2;
     }
 }
 
@@ -383,6 +392,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
             for (int cg0 = 0; cg0 < nact && !S.abort;) {
             const int cg1 = min(nact, cg0 + kCols / 16);
             const int ncols = 16 * (cg1 - cg0);
+            if (kExact)  // G scale of every output column: 2^qa x 2^qD(atom, orbital row); read after the K loop
+                for (int e = tid; e < ncols; e += kThreads) {
+                    const Atom& Y = S.at[S.act[cg0 + (e >> 4)]];
+                    const int o = e & 15;
+                    S.qd[e] = o < Y.nw ? qa_f * exp2f_i(dq_exp(__ldg(dq + 16 * Y.I + o))) : 0.f;
+                }
             // ---- K loop over active images, two images (K = 32) per step.  Warps 0-7 produce
             // A (orbital values of the step's two K images at the tile's 128 points) into
             // buffer b = step & 1 and arrive on full[b]; warp 8 fetches B and lane 0 of it
@@ -391,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
             // and the image a2 in slot s of the group, the pre-formatted tile of block
             // (I_a2, I_a1, T_a1 - T_a2) (a zero tile when the pair has no block), 512 B per
             // piece, is exactly the slot's 16-byte rows in the K-major B layout; the copies
-            // of step s + 1 start right after the MMAs of step s are issued.
+            // of step s + 1 start as soon as the MMAs of step s - 1 complete.
             const int nsteps = (nact + 1) >> 1;
             if (warp < kProdWarps) {
                 const int j = tid >> 7, pl = tid & 127;
@@ -443,13 +458,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
                         bissue[bb] += 1;
                     }
                     __syncwarp();
-                    const int per_img = (cg1 - cg0) * C::kPieces;
+                    const int per_img = cg1 - cg0;
                     for (int e = lane; e < nkk * per_img; e += 32) {
-                        const int jj = e / per_img, rem = e - jj * per_img;
-                        const int sl = rem / C::kPieces, pc = rem - sl * C::kPieces;
+                        const int jj = e / per_img, sl = e - jj * per_img;
                         const int blk = S.pairblk[S.act[kk + jj] * na + S.act[cg0 + sl]];
                         const unsigned char* src = blk >= 0 ? Dt + (int64_t)blk * kDtBytes : Dzero;
-                        tc::bulk_copy_g2s(&S.B[bb][jj][pc * kBPiece + sl * kDtPiece], src + pc * kDtPiece, kDtPiece,
+                        tc::bulk_copy_g2s(&S.B[bb][jj][sl * C::kPieces * kDtPiece], src, C::kPieces * kDtPiece,
                                           &S.bfull[bb]);
                     }
                 };
@@ -457,6 +471,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
                 for (int st = 0; st < nsteps; ++st) {
                     const int b = (chunk + st) & 1, k = 2 * st;
                     const int nk = min(2, nact - k);
+                    // B of the next step first: its buffer frees when the MMAs of step st - 1 complete,
+                    // which overlaps the producers' orbital evaluation of step st
+                    if (st + 1 < nsteps) issue_b(st + 1);
                     if (lane == 0) {
                         if (!S.abort && !tc::mbar_wait(&S.full[b], uses[b] & 1, kWait)) atomicOr(&S.abort, 1);
                         if (!S.abort) {
@@ -470,22 +487,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
                             for (int n0 = 0; n0 < ncols; n0 += 256) {
                                 const int nn = min(256, ncols - n0);
                                 const uint32_t idesc = tc::idesc_f16(128, nn, Split<H16>::bf16, 1, 0);  // A MN-major
-                                const uint32_t b_hi = bb + (n0 >> 3) * 256, b_lo = b_hi + kBPiece, b_l2 = b_lo + kBPiece;
+                                // B pieces interleaved per row group: row-group stride kSboB, piece pc at + 256 pc
+                                constexpr uint32_t kSboB = C::kPieces * 256;
+                                const uint32_t b_hi = bb + (n0 >> 3) * kSboB, b_lo = b_hi + 256, b_l2 = b_hi + 512;
                                 const uint32_t d = tmem + (uint32_t)n0;
-                                // B K-major with 16 K-columns: LBO (K-adjacent cores) 128 B, SBO (row groups) 256 B;
+                                // B K-major with 16 K-columns: LBO (K-adjacent cores) 128 B, SBO (row groups) kSboB;
                                 // A MN-major: LBO (orbital groups) kALbo, SBO (point groups) kASbo
                                 const uint32_t acc = (k + jm) > 0 ? 1u : 0u;
-                                tc::mma_f16(d, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_hi, 128, 256), idesc, acc);
+                                tc::mma_f16(d, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_hi, 128, kSboB), idesc, acc);
                                 if (kExact) {
                                     const uint32_t d1 = d + kCols;  // cross terms
-                                    tc::mma_f16(d1, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_lo, 128, 256), idesc, acc);
-                                    tc::mma_f16(d1, tc::smem_desc(a_lo, kALbo, kASbo), tc::smem_desc(b_hi, 128, 256), idesc, 1u);
-                                    tc::mma_f16(d1, tc::smem_desc(a_lo, kALbo, kASbo), tc::smem_desc(b_lo, 128, 256), idesc, 1u);
-                                    tc::mma_f16(d1, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_l2, 128, 256), idesc, 1u);
-                                    tc::mma_f16(d1, tc::smem_desc(a_l2, kALbo, kASbo), tc::smem_desc(b_hi, 128, 256), idesc, 1u);
+                                    tc::mma_f16(d1, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_lo, 128, kSboB), idesc, acc);
+                                    tc::mma_f16(d1, tc::smem_desc(a_lo, kALbo, kASbo), tc::smem_desc(b_hi, 128, kSboB), idesc, 1u);
+                                    tc::mma_f16(d1, tc::smem_desc(a_lo, kALbo, kASbo), tc::smem_desc(b_lo, 128, kSboB), idesc, 1u);
+                                    tc::mma_f16(d1, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_l2, 128, kSboB), idesc, 1u);
+                                    tc::mma_f16(d1, tc::smem_desc(a_l2, kALbo, kASbo), tc::smem_desc(b_hi, 128, kSboB), idesc, 1u);
                                 } else {
-                                    tc::mma_f16(d, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_lo, 128, 256), idesc, 1u);
-                                    tc::mma_f16(d, tc::smem_desc(a_lo, kALbo, kASbo), tc::smem_desc(b_hi, 128, 256), idesc, 1u);
+                                    tc::mma_f16(d, tc::smem_desc(a_hi, kALbo, kASbo), tc::smem_desc(b_lo, 128, kSboB), idesc, 1u);
+                                    tc::mma_f16(d, tc::smem_desc(a_lo, kALbo, kASbo), tc::smem_desc(b_hi, 128, kSboB), idesc, 1u);
                                 }
                             }
                         }
@@ -494,7 +513,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
                     }
                     __syncwarp();
                     uses[b] += 1;
-                    if (st + 1 < nsteps) issue_b(st + 1);
                 }
             }
             chunk += nsteps;
@@ -530,13 +548,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
                         // G = (exact integer part + cross terms) x 2^qa x 2^qD(atom, row)
                         float G1[16];
                         tc::tmem_ld16(ta + kCols, G1);
-                        const int* dqa = dq + 16 * Y.I;
+                        const float* qc = S.qd + c0;
 #pragma unroll
-                        for (int o = 0; o < 16; ++o) {
-                            const int orow = o - sh;  // orbital of column c0 + o within image a2
-                            const float qd = (orow >= 0 && orow < Y.nw) ? exp2f_i(dq_exp(__ldg(dqa + orow))) : 0.f;
-                            gs[o] = (Gv[o] + G1[o]) * (qa_f * qd);
-                        }
+                        for (int o = 0; o < 16; ++o) gs[o] = (Gv[o] + G1[o]) * qc[o];
                     } else {
 #pragma unroll
                         for (int o = 0; o < 16; ++o) gs[o] = Gv[o];
