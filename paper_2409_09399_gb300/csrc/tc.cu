@@ -141,6 +141,38 @@ template <> struct Conv<__nv_bfloat16> {
     static constexpr int bf16 = 1;
 };
 
+// The same splits for two values at once (the two points of a producer item), packed
+// as the 32-bit word stored for them: element of the first value in the low half.
+__device__ __forceinline__ uint32_t h2_bits(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
+__device__ __forceinline__ uint32_t b2_bits(__nv_bfloat162 h) { return *reinterpret_cast<uint32_t*>(&h); }
+template <typename H16> struct Conv2;
+template <> struct Conv2<__half> {
+    static __device__ __forceinline__ void split(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+        const __half2 h = __floats2half2_rn(x0, x1);
+        const float2 f = __half22float2(h);
+        hi = h2_bits(h);
+        lo = h2_bits(__floats2half2_rn(x0 - f.x, x1 - f.y));
+    }
+};
+template <> struct Conv2<__nv_bfloat16> {
+    static __device__ __forceinline__ void split(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+        const float2 f = __bfloat1622float2(h);
+        hi = b2_bits(h);
+        lo = b2_bits(__floats2bfloat162_rn(x0 - f.x, x1 - f.y));
+    }
+};
+// Exact form for two values: s = n + l1 + l2 (see fix_split3), packed pairs.
+__device__ __forceinline__ void fix_split3_2(float s0, float s1, uint32_t& n, uint32_t& l1, uint32_t& l2) {
+    const float n0 = rintf(s0), n1 = rintf(s1);
+    const float r0 = s0 - n0, r1 = s1 - n1;
+    const __half2 h = __floats2half2_rn(r0, r1);
+    const float2 f = __half22float2(h);
+    n = h2_bits(__floats2half2_rn(n0, n1));
+    l1 = h2_bits(h);
+    l2 = h2_bits(__floats2half2_rn(r0 - f.x, r1 - f.y));
+}
+
 // Exact form: s = n + l1 + l2 with n = rint(s) (|s| <= 128, so n is exact in
 // fp16), l1 = fp16(s - n), l2 = fp16(s - n - l1) (both differences exact in FP32).
 __device__ __forceinline__ void fix_split3(float s, unsigned short& n16, unsigned short& l1, unsigned short& l2) {
@@ -405,35 +437,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                         auto put2 = [&](int o, float va, float vb) {
                             const int r = rbase + o;
                             const int offB = kBOff + S.rowtab[r] + qoff;
-                            auto stB = [&](int pc, unsigned short x0, unsigned short x1) {
-                                *reinterpret_cast<uint32_t*>(&buf[offB + pc * kBP]) = x0 | ((uint32_t)x1 << 16);
-                            };
+                            auto st32 = [&](int off, uint32_t x) { *reinterpret_cast<uint32_t*>(&buf[off]) = x; };
                             if (kExact) {
                                 const float qi = exp2i(-sf.qeu[o]);  // unnormalised orbital values
                                 va *= qi;
                                 vb *= qi;
-                                unsigned short n0, p0, r0, n1, p1, r1;
+                                uint32_t n, p, q;
                                 if (r >= a_lo && r < a_hi) {
                                     const int offA = S.rowtab[r - a_lo] + qoff;
-                                    fix_split3(va * wa, n0, p0, r0);
-                                    fix_split3(vb * wb, n1, p1, r1);
-                                    *reinterpret_cast<uint32_t*>(&buf[offA]) = n0 | ((uint32_t)n1 << 16);
-                                    *reinterpret_cast<uint32_t*>(&buf[offA + kAP]) = p0 | ((uint32_t)p1 << 16);
-                                    *reinterpret_cast<uint32_t*>(&buf[offA + 2 * kAP]) = r0 | ((uint32_t)r1 << 16);
+                                    fix_split3_2(va * wa, vb * wb, n, p, q);
+                                    st32(offA, n); st32(offA + kAP, p); st32(offA + 2 * kAP, q);
                                 }
-                                fix_split3(va, n0, p0, r0);
-                                fix_split3(vb, n1, p1, r1);
-                                stB(0, n0, n1); stB(1, p0, p1); stB(2, r0, r1);
+                                fix_split3_2(va, vb, n, p, q);
+                                st32(offB, n); st32(offB + kBP, p); st32(offB + 2 * kBP, q);
                             } else {
-                                unsigned short ah0, al0, bh0, bl0, ah1, al1, bh1, bl1;
-                                Conv<H16>::split(va * wa, ah0, al0);
-                                Conv<H16>::split(vb * wb, ah1, al1);
-                                Conv<H16>::split(va, bh0, bl0);
-                                Conv<H16>::split(vb, bh1, bl1);
+                                uint32_t ah, al, bh, bl;
+                                Conv2<H16>::split(va * wa, vb * wb, ah, al);
+                                Conv2<H16>::split(va, vb, bh, bl);
                                 const int offA = S.rowtab[r] + qoff;
-                                *reinterpret_cast<uint32_t*>(&buf[offA]) = ah0 | ((uint32_t)ah1 << 16);
-                                *reinterpret_cast<uint32_t*>(&buf[offA + kAP]) = al0 | ((uint32_t)al1 << 16);
-                                stB(0, bh0, bh1); stB(1, bl0, bl1);
+                                st32(offA, ah); st32(offA + kAP, al);
+                                st32(offB, bh); st32(offB + kBP, bl);
                             }
                         };
                         if (!orbitals_fast2<!kExact>(sf, knot2, ax, ay, az, bx, by, bz, put2))
