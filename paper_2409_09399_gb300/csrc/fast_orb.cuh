@@ -17,6 +17,25 @@
 
 namespace gint {
 
+// Knot-table loads with L1 eviction priority "last": the table is the one
+// global data set that every producer reads again and again (streaming data
+// such as V and the pair tables is loaded with ld_stream_* and not kept in L1).
+__device__ __forceinline__ float2 ld_knot(const float2* p) {
+    float2 v;
+    asm("ld.global.nc.L1::evict_last.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double ld_stream_f64(const double* p) {
+    double v;
+    asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int ld_stream_s32(const int* p) {
+    int v;
+    asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
 struct SpeciesFast {
     int n_radial;
     int n_int;
@@ -78,7 +97,7 @@ __device__ __forceinline__ bool orbitals_fast(const SpeciesFast& s, const float2
     const float g00 = 6.f * t * (t - 1.f), g10 = t1 * (1.f - 3.f * t), g11 = t * (3.f * t - 2.f);
     const float2* kn = knot + s.knot2 + k * s.n_radial;
     for (int j = 0; j < s.n_radial; ++j) {
-        const float2 y0 = __ldg(kn + j), y1 = __ldg(kn + s.n_radial + j);  // (R, dr R') at knots k, k + 1
+        const float2 y0 = ld_knot(kn + j), y1 = ld_knot(kn + s.n_radial + j);  // (R, dr R') at knots k, k + 1
         const int l = s.rad_l[j];
         const int o = s.orb_base[j];
         float R = y0.x * h00 + y1.x * h01 + y0.y * h10 + y1.y * h11;
@@ -179,8 +198,8 @@ __device__ __forceinline__ bool orbitals_fast2(const SpeciesFast& s, const float
     const float2* kna = knot + s.knot2 + ka * s.n_radial;
     const float2* knb = knot + s.knot2 + kb * s.n_radial;
     for (int j = 0; j < s.n_radial; ++j) {
-        const float2 pa = __ldg(kna + j), qa = __ldg(kna + s.n_radial + j);
-        const float2 pb = __ldg(knb + j), qb = __ldg(knb + s.n_radial + j);
+        const float2 pa = ld_knot(kna + j), qa = ld_knot(kna + s.n_radial + j);
+        const float2 pb = ld_knot(knb + j), qb = ld_knot(knb + s.n_radial + j);
         const int l = s.rad_l[j];
         const int o = s.orb_base[j];
         float ua = (pa.x * a00 + qa.x * a01 + pa.y * a10 + qa.y * a11) * ma;

@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
             int g0, g1, g2;
             float wv = 0.f;
             if (brick_point(g, b0, b1, b2, p, g0, g1, g2))
-                wv = (float)(V[((int64_t)g0 * g.n[1] + g1) * g.n[2] + g2] * g.dV);
+                wv = (float)(ld_stream_f64(V + ((int64_t)g0 * g.n[1] + g1) * g.n[2] + g2) * g.dV);
             S.pt[p].w = p < g.bpts ? wv : 0.f;
             wmax = fmaxf(wmax, fabsf(wv));
         }
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
             const int32_t* pt = P.pairs + P.pair_start[brick];
             for (int q = tid; q < na * na; q += kTcThreads) {
                 const int a1 = q / na, a2 = q - a1 * na;
-                if (a1 <= a2) S.pairblk[pair_index(a1, a2)] = __ldg(pt + q);
+                if (a1 <= a2) S.pairblk[pair_index(a1, a2)] = ld_stream_s32(pt + q);
             }
         }
         // zero the padding rows [nrow, round128(nrow)) of both chunk buffers (B pieces; A pieces

@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
                 int g0, g1, g2;
                 float wv = 0.f;
                 if (brick_point(g, b0, b1, b2, p, g0, g1, g2))
-                    wv = (float)(2.0 * V[((int64_t)g0 * g.n[1] + g1) * g.n[2] + g2] * g.dV);
+                    wv = (float)(2.0 * ld_stream_f64(V + ((int64_t)g0 * g.n[1] + g1) * g.n[2] + g2) * g.dV);
                 S.W2[p] = wv;
             }
         }
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
             const int32_t* pt = P.pairs + P.pair_start[brick];
             for (int q = tid; q < na * na; q += kThreads) {
                 const int a1 = q / na, a2 = q - a1 * na;
-                S.pairblk[q] = __ldg(pt + a2 * na + a1);
+                S.pairblk[q] = ld_stream_s32(pt + a2 * na + a1);
             }
         }
         __syncthreads();
