@@ -170,6 +170,17 @@ gint_status gint_force_stress(gint_handle* h, const double* V, const double* D, 
  *   - Calls no cudaMalloc, cudaFree or other allocating routine. */
 gint_status gint_vlocal_static(gint_handle* h, const double* V, double* H, gint_stream stream);
 
+/* Bloch sum of H^V (the step after the grid integrals, Section 2.4 setting):
+ *   H(k)_{I mu, J nu} = sum over pattern blocks (I, J, t) of exp(2 pi i k . t) H_IJ(t)[mu, nu],
+ * k given in fractions of the reciprocal lattice vectors (k . T = 2 pi kfrac . t).
+ * H: device, the full block list (as gint_vlocal writes it).  Hk: device, dense
+ * n_orbitals x n_orbitals complex matrix, row-major with leading dimension ld (complex
+ * elements, ld >= n_orbitals), real and imaginary parts interleaved (complex128); rows
+ * and columns in atom order, each atom's orbitals in the pattern's order.  Hk is
+ * overwritten.  Asynchronous on `stream`; host validation only. */
+gint_status gint_fold_k(const gint_handle* h, const double* H, const double kfrac[3], double* Hk, int64_t ld,
+                        gint_stream stream);
+
 /* Whether the kernels of the handle's current precision accept its bricks
  * (the tensor-core forms bound the orbitals, atom images and points of one
  * brick).  GINT_OK, or GINT_ERR_UNSUPPORTED with the limits in
@@ -211,6 +222,7 @@ typedef struct {
     int brick[3];
     int precision;
     int64_t scratch_bytes;        /* device scratch owned by the handle */
+    int64_t n_orbitals;           /* sum over atoms of their orbitals: the dimension of H(k) */
 } gint_info;
 
 gint_status gint_get_info(const gint_handle* h, gint_info* info);

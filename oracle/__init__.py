@@ -192,6 +192,25 @@ class Oracle:
             raise RuntimeError("oracle force: neighbour pair missing from the pattern")
         return F, W.reshape(-1, 3, 3)
 
+    def fold_k(self, H, kfrac):
+        """Bloch sum H(k) = sum over blocks (I, J, t) of exp(2 pi i k . t) H_IJ(t) (Eq. 6-8 setting).
+
+        k = sum_i kfrac_i b_i with b_i the reciprocal vectors (b_i . a_j = 2 pi delta_ij), so
+        k . T = 2 pi kfrac . t for T = t . A.  Dense N x N complex matrix, N = sum of orbitals;
+        rows and columns in atom order, each atom's orbitals in the pattern's order.
+        """
+        H = np.asarray(H, dtype=np.float64)
+        kf = np.asarray(kfrac, dtype=np.float64).reshape(3)
+        off = np.concatenate([[0], np.cumsum(self.nw)]).astype(np.int64)
+        N = int(off[-1])
+        Hk = np.zeros((N, N), dtype=np.complex128)
+        for b in range(self.blocks.shape[0]):
+            I, J = int(self.blocks[b, 0]), int(self.blocks[b, 1])
+            t = self.blocks[b, 2:5].astype(np.float64)
+            ph = np.exp(2j * np.pi * float(kf @ t))
+            Hk[off[I]:off[I + 1], off[J]:off[J + 1]] += ph * self.block(H, b)
+        return Hk
+
     def stress(self, V, D):
         F, W = self.force(V, D)
         return -W.sum(0) / self.omega, F

@@ -155,6 +155,7 @@ struct gint_handle {
     int64_t n_ext = 0;
     int64_t n_blocks = 0;
     int64_t n_values = 0;
+    int64_t n_orbitals = 0;           // sum of the atoms' orbitals (dimension of H(k))
     int64_t n_brick_atoms = 0;
     int64_t n_brick_pairs = 0;
     int max_brick_atoms = 0;
@@ -178,6 +179,7 @@ struct gint_handle {
     int* d_err = nullptr;             // [0] device check flags, [2] work counter
     int* d_nw_atom = nullptr;         // orbitals of every atom
     int* d_atom_sp = nullptr;         // species of every atom
+    int64_t* d_orb_off = nullptr;     // first orbital (dense row) of every atom, n_atoms + 1
     double* d_facc = nullptr;         // per-atom force and virial accumulators, n_atoms x 12
     double* d_red = nullptr;          // small FP64 reduction buffer ([0] energy)
     void* d_dt = nullptr;             // per-call 16x16 tensor-core copy of D (1 KB per block)

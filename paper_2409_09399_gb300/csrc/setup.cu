@@ -712,6 +712,10 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
         for (int i = 0; i < n_atoms; ++i) nwa[i] = nw_sp[spc[i]];
         GINT_TRY(dev_upload(&h->d_nw_atom, nwa.data(), nwa.size()));
         GINT_TRY(dev_upload(&h->d_atom_sp, spc.data(), spc.size()));
+        std::vector<int64_t> oo(n_atoms + 1, 0);
+        for (int i = 0; i < n_atoms; ++i) oo[i + 1] = oo[i] + nwa[i];
+        h->n_orbitals = oo[n_atoms];
+        GINT_TRY(dev_upload(&h->d_orb_off, oo.data(), oo.size()));
     }
     GINT_CUDA_TRY(cudaMalloc(&h->d_mirror, sizeof(int32_t) * std::max<int64_t>(1, h->n_blocks)));
     {
@@ -856,7 +860,7 @@ static void free_handle(gint_handle* h) {
     cudaSetDevice(h->device);
     void* ptrs[] = {h->d_sp, h->d_coef64, h->d_coef32, h->d_knot32, h->d_ext, h->d_blocks, h->d_offsets, h->d_row_start,
                     h->d_mirror, h->d_brick_start, h->d_brick_atoms, h->d_work, h->d_pair_start, h->d_pairs, h->d_empty, h->d_err, h->d_red,
-                    h->d_scratch, h->d_nw_atom, h->d_atom_sp, h->d_facc, h->d_dt, h->d_dq, h->d_zero};
+                    h->d_scratch, h->d_nw_atom, h->d_atom_sp, h->d_orb_off, h->d_facc, h->d_dt, h->d_dq, h->d_zero};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (prev >= 0) cudaSetDevice(prev);
@@ -983,6 +987,7 @@ gint_status gint_get_info(const gint_handle* h, gint_info* info) {
     for (int i = 0; i < 3; ++i) info->brick[i] = h->grid.B[i];
     info->precision = h->precision;
     info->scratch_bytes = (int64_t)h->scratch_bytes;
+    info->n_orbitals = h->n_orbitals;
     return GINT_OK;
 }
 

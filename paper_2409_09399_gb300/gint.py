@@ -22,7 +22,7 @@ STATUS = {0: "GINT_OK", 1: "GINT_ERR_INVALID_ARG", 2: "GINT_ERR_CUDA", 3: "GINT_
 
 # exported symbols, in the order include/gint.h declares them
 SYMBOLS = ["gint_setup", "gint_destroy", "gint_pattern", "gint_set_precision", "gint_vlocal", "gint_rho",
-           "gint_force_stress", "gint_vlocal_static", "gint_check", "gint_batch_create", "gint_batch_run",
+           "gint_force_stress", "gint_vlocal_static", "gint_check", "gint_fold_k", "gint_batch_create", "gint_batch_run",
            "gint_batch_destroy", "gint_sync", "gint_get_info", "gint_work_stats", "gint_last_error"]
 
 
@@ -51,7 +51,8 @@ class _Info(ctypes.Structure):
                 ("n_bricks", ctypes.c_int64), ("n_bricks_nonempty", ctypes.c_int64),
                 ("n_brick_atoms", ctypes.c_int64), ("n_brick_pairs", ctypes.c_int64),
                 ("max_brick_atoms", ctypes.c_int), ("max_brick_orbitals", ctypes.c_int),
-                ("brick", ctypes.c_int * 3), ("precision", ctypes.c_int), ("scratch_bytes", ctypes.c_int64)]
+                ("brick", ctypes.c_int * 3), ("precision", ctypes.c_int), ("scratch_bytes", ctypes.c_int64),
+                ("n_orbitals", ctypes.c_int64)]
 
 
 _lib = None
@@ -84,6 +85,8 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.gint_force_stress.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     L.gint_vlocal_static.restype = i32
     L.gint_vlocal_static.argtypes = [vp, vp, vp, vp]
+    L.gint_fold_k.restype = i32
+    L.gint_fold_k.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double * 3), vp, i64, vp]
     L.gint_check.restype = i32
     L.gint_check.argtypes = [vp]
     L.gint_batch_create.restype = i32
@@ -172,6 +175,7 @@ class Gint:
         nb, nv = ctypes.c_int64(), ctypes.c_int64()
         _check(L.gint_pattern(self._h, ctypes.byref(nb), ctypes.byref(nv), None, None))
         self.n_blocks, self.n_values = nb.value, nv.value
+        self.n_orbitals = int(self.nw.sum())
         self._pattern = None
 
     # -------------------------------------------------------------- basics
@@ -189,6 +193,21 @@ class Gint:
     def set_precision(self, precision):
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         _check(load().gint_set_precision(self._h, p))
+
+    def fold_k(self, H, kfrac, Hk=None, stream=None):
+        """Bloch sum H(k) = sum_t exp(2 pi i kfrac . t) H(t): dense complex128 CUDA tensor (N, N)."""
+        import torch
+        self._need(H, self.n_values, "H")
+        n = self.n_orbitals
+        if Hk is None:
+            Hk = torch.empty((n, n), dtype=torch.complex128, device=H.device)
+        if not (Hk.is_cuda and Hk.dtype == torch.complex128 and Hk.dim() == 2 and Hk.shape[0] >= n
+                and Hk.shape[1] >= n and Hk.stride(1) == 1):
+            raise TypeError("Hk must be a row-major complex128 CUDA matrix of at least n_orbitals x n_orbitals")
+        k = (ctypes.c_double * 3)(*[float(x) for x in kfrac])
+        _check(load().gint_fold_k(self._h, _ptr(H), ctypes.byref(k), Hk.data_ptr(), Hk.stride(0),
+                                  self._stream(stream)))
+        return Hk
 
     def supported(self) -> bool:
         """Whether the kernels of the current precision accept this handle's bricks."""
