@@ -97,6 +97,8 @@ template <bool kExact> struct TcSmem {
     unsigned short rowtab[C::kRows];  // byte offset of row r's 16-byte segment in a piece
     double row_s[C::kRows];           // exact form: [ylm_norm x] 2^qeu of row r (FP64)
     float row_f[C::kRows];            // exact form: 2^qeu of row r
+    unsigned char need_list[kTcMaxAtoms];  // atom images with rows the current pass reads
+    int n_need;
     unsigned char seg_tile[kTcMaxSeg];  // segment: row tile, columns [c0, c1), TMEM column
     short seg_c0[kTcMaxSeg], seg_c1[kTcMaxSeg], seg_tcol[kTcMaxSeg];
     int pass_first[kTcMaxSeg + 1];      // first segment of each pass
@@ -386,20 +388,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
         const int nchunks = g.bpad / kTcChunk;
         for (int pass = 0; pass < npass && !S.abort; ++pass) {
             const int s0p = S.pass_first[pass], s1p = S.pass_first[pass + 1];
-            const int row_lo = 128 * S.seg_tile[s0p];  // rows below this are not read in this pass
+            const int t_lo = 128 * S.seg_tile[s0p], t_hi = 128 * (S.seg_tile[s1p - 1] + 1);
             // exact form: A pieces hold rows [a_lo, a_hi) of this pass's row tiles (<= 384 rows)
-            const int a_lo = kExact ? row_lo : 0;
-            const int a_hi = kExact ? 128 * (S.seg_tile[s1p - 1] + 1) : C::kRows;
-            if (kExact) {
+            const int a_lo = kExact ? t_lo : 0;
+            const int a_hi = kExact ? t_hi : C::kRows;
+            // the pass reads A rows of its row tiles [t_lo, t_hi) and B rows of its segments'
+            // column ranges; only atom images with rows there are evaluated (listed by warp 0)
+            if (warp == 0) {
+                uint64_t m = 0;
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int a = lane + 32 * h2;
+                    bool nd = false;
+                    if (a < na) {
+                        const int r0 = S.at[a].off, r1 = r0 + S.at[a].nw;
+                        nd = r0 < t_hi && r1 > t_lo;
+                        for (int sg = s0p; sg < s1p; ++sg) nd = nd || (r0 < S.seg_c1[sg] && r1 > S.seg_c0[sg]);
+                    }
+                    m |= (uint64_t)__ballot_sync(0xffffffffu, nd) << (32 * h2);
+                }
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int a = lane + 32 * h2;
+                    if (a < na && (m >> a & 1ull)) S.need_list[__popcll(m & ((1ull << a) - 1ull))] = (unsigned char)a;
+                }
+                if (lane == 0) S.n_need = __popcll(m);
+            }
+            {
                 // zero A rows [max(nrow, a_lo), a_hi) (they may hold rows of the previous pass;
                 // every MMA of that pass has completed)
                 const int z0 = max(nrow, a_lo);
-                for (int b = 0; b < 2; ++b)
-                    for (int e = tid; e < (a_hi - z0) * kTcChunk; e += kTcThreads) {
-                        const int r = z0 - a_lo + e / kTcChunk, q = e % kTcChunk;
-                        const int o = piece_off(r, q);
-                        for (int pc = 0; pc < C::kPieces; ++pc) *reinterpret_cast<unsigned short*>(&S.buf[b][pc * kAP + o]) = 0;
-                    }
+                if (kExact)
+                    for (int b = 0; b < 2; ++b)
+                        for (int e = tid; e < (a_hi - z0) * kTcChunk; e += kTcThreads) {
+                            const int r = z0 - a_lo + e / kTcChunk, q = e % kTcChunk;
+                            const int o = piece_off(r, q);
+                            for (int pc = 0; pc < C::kPieces; ++pc) *reinterpret_cast<unsigned short*>(&S.buf[b][pc * kAP + o]) = 0;
+                        }
                 __syncthreads();
             }
             if (!issuer_warp) {
@@ -409,18 +432,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                 for (int c = b; c < nchunks; c += 2) {
                     if (uses[b] > 0 && !S.abort && !tc::mbar_wait(&S.empty[b], (uses[b] - 1) & 1, kWaitLimit))
                         atomicOr(&S.abort, 1);
-                    // orbital values at the chunk's points, two points per item, for atom
-                    // images with rows this pass reads.  Item bits: [1:0] point pair within a
-                    // half chunk, [4:2] atom within a group of 8, [5] half chunk, [6..] atom
-                    // group; so a warp stores 8 atoms (distinct rows mod 8) x 4 point pairs of
-                    // the same 16-byte row segment half: 32 different banks.
-                    const int n_items = ((na + 7) >> 3) << 6;
+                    // orbital values at the chunk's points, two points per item, for the atom
+                    // images of need_list.  Item bits: [1:0] point pair within a half chunk,
+                    // [4:2] list entry within a group of 8, [5] half chunk, [6..] group; so a
+                    // warp stores 8 atoms (distinct rows mod 8) x 4 point pairs of the same
+                    // 16-byte row segment half: 32 different banks.
+                    const int n_need = S.n_need;
+                    const int n_items = ((n_need + 7) >> 3) << 6;
                     for (int item = lt; item < n_items; item += kTcHalf) {
-                        const int a = ((item >> 6) << 3) | ((item >> 2) & 7);
+                        const int k = ((item >> 6) << 3) | ((item >> 2) & 7);
                         const int qp = (((item >> 5) & 1) << 2) | (item & 3);
-                        if (a >= na) continue;
-                        const TcAtom& X = S.at[a];
-                        if (X.off + X.nw <= row_lo) continue;
+                        if (k >= n_need) continue;
+                        const TcAtom& X = S.at[S.need_list[k]];
                         const int q = 2 * qp;
                         const int p = c * kTcChunk + q;
                         const float4 u4 = S.pt[p], v4 = S.pt[p + 1];

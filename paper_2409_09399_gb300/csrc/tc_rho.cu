@@ -40,7 +40,9 @@ namespace gint {
 
 namespace {
 constexpr int kProdWarps = 8;                    // orbital-value producers and epilogue
-constexpr int kThreads = 32 * kProdWarps + 32;   // + one warp for B copies and MMA issue
+constexpr int kCopyWarp = kProdWarps;            // bulk copies of B
+constexpr int kMmaWarp = kProdWarps + 1;         // MMA issue (one thread)
+constexpr int kThreads = 32 * kProdWarps + 64;
 constexpr int kMaxAtoms = 64;
 constexpr int kMaxCols = 512;            // TMEM columns (packed orbitals of one M-tile)
 // A pieces (128 points x 16 orbital slots) are MN-major: core matrix (point group
@@ -123,9 +125,6 @@ template <> struct Split<__nv_bfloat16> {
     static constexpr int bf16 = 1;
 };
 
-// byte offset of element (row r, k) in a K-major piece with 16 K-columns:
-// core (r/8, k/8) at ((r/8)*2 + k/8)*128, row r%8 at *16, column k%8 at *2
-__device__ __forceinline__ int kmaj16(int r, int k) { return ((((r >> 3) << 1) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1); }
 // Pre-formatted D tile of one block (16 x 16, K-major core matrices): the pieces
 // are interleaved per group of 8 rows, [rows 0-7: piece 0, 1(, 2)][rows 8-15: ...],
 // 256 B per (row group, piece), so a tile is one contiguous copy into its image
@@ -241,7 +240,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem<kExact>& S = *reinterpret_cast<Smem<kExact>*>(smem_raw);
     using C = RfCfg<kExact>;
-    constexpr int kBPiece = C::kBPiece;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const CellJob* Jc = &J_in;  // problem and buffers of the current item
     int cur_cell = -1;
@@ -277,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
     if (kExact && !kMulti) set_qa(J_in.P);
     uint32_t uses[2] = {0, 0};  // steps that used buffer b (every thread counts them)
     uint32_t dones = 0;         // completed phases of done
-    uint32_t bissue[2] = {0, 0}, bdone[2] = {0, 0};  // warp 8 lane 0: bulk-copy phases started / waited
+    uint32_t bissue[2] = {0, 0};  // copy warp: bulk-copy phases started per buffer
     uint32_t chunk = 0;  // global chunk counter (buffer parity)
 
     for (;;) {
@@ -447,9 +445,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
                     tc::mbar_arrive(&S.full[b]);
                     uses[b] += 1;
                 }
-            } else {
-                // warp 8: B copies (all lanes) and MMA issue (lane 0)
-                auto issue_b = [&](int st) {
+            } else if (warp == kCopyWarp) {
+                // B copies of every step; buffer b is refilled once the MMAs of the step
+                // that last read it have completed (empty[b])
+                for (int st = 0; st < nsteps; ++st) {
                     const int bb = (chunk + st) & 1, kk = 2 * st;
                     const int nkk = min(2, nact - kk);
                     if (lane == 0) {
@@ -466,20 +465,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
                         tc::bulk_copy_g2s(&S.B[bb][jj][sl * C::kPieces * kDtPiece], src, C::kPieces * kDtPiece,
                                           &S.bfull[bb]);
                     }
-                };
-                issue_b(0);
+                    uses[bb] += 1;
+                }
+            } else {
+                // MMA issue: one thread waits for A (full) and B (bfull) of each step, issues
+                // its MMAs and commits empty[b]; it never waits for earlier MMAs, so the
+                // tensor pipe has the next step queued while the current one runs
                 for (int st = 0; st < nsteps; ++st) {
                     const int b = (chunk + st) & 1, k = 2 * st;
                     const int nk = min(2, nact - k);
-                    // B of the next step first: its buffer frees when the MMAs of step st - 1 complete,
-                    // which overlaps the producers' orbital evaluation of step st
-                    if (st + 1 < nsteps) issue_b(st + 1);
                     if (lane == 0) {
                         if (!S.abort && !tc::mbar_wait(&S.full[b], uses[b] & 1, kWait)) atomicOr(&S.abort, 1);
-                        if (!S.abort) {
-                            if (tc::mbar_wait(&S.bfull[b], uses[b] & 1, kWait)) bdone[b] += 1;
-                            else atomicOr(&S.abort, 1);
-                        }
+                        if (!S.abort && !tc::mbar_wait(&S.bfull[b], uses[b] & 1, kWait)) atomicOr(&S.abort, 1);
                         tc::fence_after_sync();
                         for (int jm = 0; jm < nk && !S.abort; ++jm) {
                             const uint32_t a_hi = tc::smem_u32(S.A[b][jm]), a_lo = a_hi + kAPiece, a_l2 = a_lo + kAPiece;
@@ -614,12 +611,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
     __syncthreads();
     // no MMA or bulk copy may be in flight when tensor memory and shared memory are released:
     // one more commit (completes after every earlier MMA) and the copies not yet waited for
-    if (warp == kProdWarps && lane == 0) {
+    if (warp == kMmaWarp && lane == 0) {
         tc::mma_commit(&S.done);
         (void)tc::mbar_wait(&S.done, dones & 1, kWait);
-        for (int b = 0; b < 2; ++b)
-            if (bissue[b] > bdone[b]) (void)tc::mbar_wait(&S.bfull[b], bdone[b] & 1, kWait);
     }
+    if (warp == kCopyWarp && lane == 0)  // the last phase of each buffer covers every earlier copy
+        for (int b = 0; b < 2; ++b)
+            if (bissue[b] > 0) (void)tc::mbar_wait(&S.bfull[b], (bissue[b] - 1) & 1, kWait);
     if (S.abort && tid == 0) atomicOr(Jc->P.err, kErrTimeout);
     tc::fence_before_sync();
     __syncthreads();
