@@ -145,6 +145,38 @@ def oracle_sample(system, n_points, n_blocks, n_atoms_f, seed=11, inputs=None):
     return full, desc, samples
 
 
+CALLS = ("vlocal", "rho", "force")
+TC_PRODUCTS = {"fp16x3": 3, "bf16x3": 3, "fp16x4": 6}  # 16-bit tensor products per credited product
+DTYPES = {"fp64": "f64", "fp32": "f32", "fp16x3": "f16x3", "bf16x3": "bf16x3", "fp16x4": "f16x4"}
+
+
+def parse_forms(spec):
+    """'fp16x4' (every call) or 'vlocal=fp16x4,rho=fp16x4,force=fp16x3' (one form per call)."""
+    if "=" not in spec:
+        return {c: spec for c in CALLS}
+    forms = {}
+    for item in spec.split(","):
+        k, v = item.split("=")
+        if k not in CALLS:
+            raise SystemExit(f"--precision: unknown call {k!r} (expected one of {CALLS})")
+        forms[k] = v
+    if set(forms) != set(CALLS):
+        raise SystemExit(f"--precision: give a form for each of {CALLS}")
+    return forms
+
+
+def launches_per_step(forms):
+    """Kernels of ours per step: the call's kernel, plus the mirror (and, exact form, the
+    normalisation) after H^V; the D row maxima (exact form) and D format before the
+    tensor-core rho and force kernels; the empty-brick fill after rho; the finalize after force."""
+    tc = lambda f: f in TC_PRODUCTS  # noqa: E731
+    ex = lambda f: f == "fp16x4"  # noqa: E731
+    n = 2 + ex(forms["vlocal"])
+    n += 2 + tc(forms["rho"]) + ex(forms["rho"])
+    n += 2 + tc(forms["force"]) + ex(forms["force"])
+    return int(n)
+
+
 def sample_errors(samples, H, rho, F, blocks, offsets):
     """Errors of GPU results against the oracle's sampled outputs (same pattern order)."""
     import numpy as np
@@ -211,7 +243,9 @@ def run_ours(args):
     desc, m = WORKLOADS[args.workload]
     system = synth.tbg(m)
     ng = system.n_grid
-    prec = args.precision
+    forms = parse_forms(args.precision)
+    prec = forms["vlocal"]
+    mixed_forms = len(set(forms.values())) > 1
     torch.cuda.synchronize()
     t_setup0 = time.perf_counter()
     g = gint.from_system(system, precision=prec, brick=tuple(args.brick), device=local)
@@ -231,15 +265,23 @@ def run_ours(args):
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     n_ev = 4
 
+    def use(call):
+        # the form of each call (a host-side field of the handle; no device work)
+        if mixed_forms:
+            g.set_precision(forms[call])
+
     def step(record=None):
         if record is not None:
             record[0].record(stream)
+        use("vlocal")
         g.vlocal(V, H, stream=stream)
         if record is not None:
             record[1].record(stream)
+        use("rho")
         g.rho(D, rho, stream=stream)
         if record is not None:
             record[2].record(stream)
+        use("force")
         g.force_stress(V, D, out=(F, sig, vir, E), stream=stream)
         if record is not None:
             record[3].record(stream)
@@ -285,7 +327,10 @@ def run_ours(args):
 
     # ---- FP64 form on the same GPU (one step, same inputs)
     fp64 = None
-    if args.fp64_steps > 0 and prec != "fp64":
+    if args.fp64_steps > 0 and set(forms.values()) != {"fp64"}:
+        saved, mixed_saved = dict(forms), mixed_forms
+        forms.update({c: "fp64" for c in CALLS})
+        mixed_forms = False
         g.set_precision("fp64")
         step()
         g.sync()
@@ -301,6 +346,8 @@ def run_ours(args):
         fp64 = {"value": ng / (ms64 / 1e3), "unit": "grid_points/s", "ms_per_step": ms64,
                 "speedup_of_mixed": ms64 / ms_per_step}
         H_fp64, rho_fp64, F_fp64 = H.clone(), rho.clone(), F.clone()
+        forms.update(saved)
+        mixed_forms = mixed_saved
         g.set_precision(prec)
 
     # ---- end to end through the public API with host buffers
@@ -319,8 +366,11 @@ def run_ours(args):
         def e2e_step():
             Vd.copy_(Vh, non_blocking=True)
             Dd.copy_(Dh, non_blocking=True)
+            use("vlocal")
             g.vlocal(Vd, H, stream=stream)
+            use("rho")
             g.rho(Dd, rho, stream=stream)
+            use("force")
             g.force_stress(Vd, Dd, out=(F, sig, vir, E), stream=stream)
             Hh.copy_(H, non_blocking=True)
             rhoh.copy_(rho, non_blocking=True)
@@ -354,9 +404,10 @@ def run_ours(args):
     dom = int(np.argmax(parts))
     dom_name = names[dom]
     achieved = flops[dom_name] / (parts[dom] / 1e3) / 1e12
-    if prec == "fp64":
+    dom_prec = forms[dom_name]
+    if dom_prec == "fp64":
         peak, bound, src = 1.25, "alu", "FP64 1.25 TFLOP/s nominal (DFMA; recipe table)"
-    elif prec == "fp32":
+    elif dom_prec == "fp32":
         peak, bound = 152 * 128 * 2 * 2.07e9 / 1e12, "alu"
         src = "FP32 FFMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
     else:
@@ -364,7 +415,7 @@ def run_ours(args):
         peak, bound = peaks.get("bf16_tflops_sustained", 1711.1), "tensor"
         src = f"16-bit dense tensor, sustained ({peak_src} bf16 cuBLAS loop)"
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", f"traffic_{dom_name}_{prec}.json")
+    tpath = os.path.join(ROOT, "profiles", f"traffic_{dom_name}_{dom_prec}.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
             tj = json.load(f)
@@ -381,7 +432,7 @@ def run_ours(args):
             "traffic": traffic, "kernel": dom_name, "peak_source": src,
             "algorithmic_flop_per_launch": flops[dom_name]}
     # split forms issue k 16-bit products per credited product: the fraction against peak / k
-    k_products = {"fp16x3": 3, "bf16x3": 3, "fp16x4": 6}.get(prec)
+    k_products = TC_PRODUCTS.get(dom_prec)
     if k_products:
         roof["products_per_flop"] = k_products
         roof["frac_of_peak_over_products"] = achieved / (peak / k_products)
@@ -394,28 +445,27 @@ def run_ours(args):
         t_full, sample, samples = oracle_sample(system, args.ref_points, args.ref_blocks, args.ref_atoms)
         cpu = {"value": ng / t_full, "unit": "grid_points/s", "cores": oracle.num_threads(), "kind": "oracle",
                "sample": json.dumps(sample)}
-        errors = {prec: sample_errors(samples, H_mixed, rho_mixed, F_mixed, blocks, offsets)}
+        errors = {args.precision: sample_errors(samples, H_mixed, rho_mixed, F_mixed, blocks, offsets)}
         if fp64 is not None:
             errors["fp64"] = sample_errors(samples, H_fp64, rho_fp64, F_fp64, blocks, offsets)
         errors["sample"] = "oracle outputs at the cpu_baseline sample (random points, blocks, atoms)"
 
-    # vlocal kernel + mirror; rho (+ D format on the tensor path) + empty-brick fill; force (+ D format) + finalize;
-    # the exact form adds a row-maximum pass over D before each D format
-    launches_per_step = {"fp64": 6, "fp32": 6, "fp16x4": 10}.get(prec, 8)
     gb = lambda n: f"{n * 8 / 1e9:.1f} GB"  # noqa: E731
     l2_note = (f"inputs larger than L2 (V {gb(ng)}, rho {gb(ng)}, D {gb(g.n_values)})" if ng * 8 > 256e6 else
                f"V {gb(ng)}, rho {gb(ng)}, D {gb(g.n_values)}: not larger than L2 (profiling / test size)")
     line = {"metric": METRIC, "value": value, "unit": "grid_points/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16x3": "f16x3", "bf16x3": "bf16x3", "fp16x4": "f16x4"}.get(prec, prec),
+            "vs_baseline": None,
+            "dtype": ",".join(dict.fromkeys(DTYPES.get(forms[c], forms[c]) for c in CALLS)),
             "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "grid": list(system.grid),
-                       "grid_points": ng, "atoms": system.n_atoms, "precision": prec,
+                       "grid_points": ng, "atoms": system.n_atoms,
+                       "precision": forms if mixed_forms else prec,
                        "brick": list(info["brick"]), "l2": l2_note,
                        "parallelism": "replicas" if ws > 1 else "single", "setup_s": t_setup},
             "ms_per_call": {"vlocal": parts[0], "rho": parts[1], "force_stress": parts[2]},
             "fp64_form": fp64, "errors_vs_oracle": errors, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
-            "clocks": clocks.summary(), "gpu_launches": launches_per_step * args.steps}
+            "clocks": clocks.summary(), "gpu_launches": launches_per_step(forms) * args.steps}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -497,6 +547,8 @@ def main():
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.workload.startswith("batch"):
+        if "=" in args.precision:
+            raise SystemExit("--precision: the batched workload takes one form for every call")
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no oracle timing arm"}))
             return 0

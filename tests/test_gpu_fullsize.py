@@ -11,10 +11,12 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-# stated accuracy of each form (max abs for H and F, normwise for rho over the sample)
+# stated accuracy of each form (max abs for H and F, normwise for rho over the sample).
+# The three-product form meets the force target F <= 1e-5 Ha/bohr (not the H or rho
+# targets), so a step may take its forces from it.
 TOL = {
     "fp64": {"H": 1e-11, "rho": 1e-11, "F": 1e-10},
-    "fp16x3": {"H": 5e-5, "rho": 5e-5, "F": 5e-5},
+    "fp16x3": {"H": 5e-5, "rho": 5e-5, "F": 1e-5},
     "fp16x4": {"H": 1e-7, "rho": 1e-6, "F": 1e-5},
 }
 

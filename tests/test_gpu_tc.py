@@ -14,7 +14,7 @@ _cache = {}
 # exact form (fp16x4) meets the target accuracy H <= 1e-7 Ha, rho <= 1e-6
 # (normwise), F <= 1e-5 Ha/bohr.
 TOL = {
-    "fp16x3": {"H": 5e-5, "rho": 1e-4, "F": 1e-4, "sigma": 1e-4},
+    "fp16x3": {"H": 5e-5, "rho": 1e-4, "F": 1e-5, "sigma": 1e-4},
     "bf16x3": {"H": 5e-5, "rho": 1e-4, "F": 1e-4, "sigma": 1e-4},
     "fp16x4": {"H": 1e-7, "rho": 1e-6, "F": 1e-5, "sigma": 1e-6},
 }
