@@ -9,6 +9,11 @@ value = grid points x steps / time (all ranks).  Inputs stay resident in HBM
 during the timed steps; V (5.1 GB) and rho (5.1 GB) exceed L2, so no flush is
 needed between steps.
 
+Each call takes the cheapest tensor-core form that meets its stated error
+(H <= 1e-7 Ha, rho <= 1e-6 normwise, F <= 1e-5 Ha/bohr): the exact form
+(fp16x4) for H^V and rho, the three-product form (fp16x3) for the force
+(--precision picks one form for all calls, or one per call).
+
 --impl reference times the FP64 oracle (oracle/, plain C + OpenMP) on the
 host cores on a bounded sample of the same workload.
 """
@@ -33,6 +38,7 @@ WORKLOADS = {
     "tbg_m10": ("twisted bilayer graphene m=10, 1324 C atoms, DZP, rc 7 bohr, h=pi/20 bohr", 10),
     "tbg_m5": ("twisted bilayer graphene m=5, 364 C atoms, DZP, rc 7 bohr, h=pi/20 bohr", 5),
 }
+DEFAULT_FORMS = "vlocal=fp16x4,rho=fp16x4,force=fp16x3"
 METRIC = "grid pts/s for gint H^V+rho(+force), mixed vs FP64 form at stated error, TBG 10,444"
 
 
@@ -535,7 +541,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch256", "batch64"], default="tbg_m29")
-    ap.add_argument("--precision", default="fp16x4")
+    ap.add_argument("--precision", default=None,
+                    help=f"one form for every call, or one per call (default {DEFAULT_FORMS}; batches: fp16x4)")
     ap.add_argument("--brick", type=int, nargs=3, default=[0, 0, 0])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -544,6 +551,8 @@ def main():
     ap.add_argument("--ref-blocks", type=int, default=24)
     ap.add_argument("--ref-atoms", type=int, default=1)
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "fp16x4" if args.workload.startswith("batch") else DEFAULT_FORMS
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.workload.startswith("batch"):
