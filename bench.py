@@ -428,8 +428,8 @@ def run_ours(args):
         # DRAM bytes from an ncu capture, valid only while the kernel sources it was taken on are unchanged
         import hashlib
         hs = hashlib.sha256()
-        for src in tj.get("sources", []):
-            with open(os.path.join(ROOT, src), "rb") as f:
+        for path in tj.get("sources", []):
+            with open(os.path.join(ROOT, path), "rb") as f:
                 hs.update(f.read())
         if tj.get("workload_scaled_to", tj.get("scaled_to", {}).get("workload")) == args.workload and \
                 hs.hexdigest() == tj.get("source_sha256"):

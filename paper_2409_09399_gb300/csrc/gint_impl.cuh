@@ -98,6 +98,7 @@ struct Problem {
     const int32_t* work;         // non-empty brick ids, natural order
     const int64_t* pair_start;   // n_bricks + 1: first entry of each brick's pair table
     const int32_t* pairs;        // per brick, na x na: block (I_a, I_b, t_b - t_a) of images a, b, -1 if none
+    const unsigned long long* tile_mask;  // per work item and 128-point tile: images within rc of a tile point
     int n_work;
     const int32_t* blocks;       // n_blocks x 5
     const int64_t* offsets;      // n_blocks + 1
@@ -175,6 +176,7 @@ struct gint_handle {
     int32_t* d_work = nullptr;        // non-empty bricks
     int64_t* d_pair_start = nullptr;  // per-brick pair tables (see Problem::pairs)
     int32_t* d_pairs = nullptr;
+    unsigned long long* d_tile_mask = nullptr;  // see Problem::tile_mask
     int32_t* d_empty = nullptr;       // empty bricks
     int* d_err = nullptr;             // [0] device check flags, [2] work counter
     int* d_nw_atom = nullptr;         // orbitals of every atom
@@ -203,6 +205,7 @@ struct gint_handle {
         p.work = d_work;
         p.pair_start = d_pair_start;
         p.pairs = d_pairs;
+        p.tile_mask = d_tile_mask;
         p.n_work = (int)n_work;
         p.blocks = d_blocks;
         p.offsets = d_offsets;
@@ -395,6 +398,47 @@ __device__ __forceinline__ void brick_coords(const GridDev& g, int b, int& b0, i
     b2 = b % g.nb[2];
     b1 = (b / g.nb[2]) % g.nb[1];
     b0 = b / (g.nb[2] * g.nb[1]);
+}
+
+// The three helpers below fix every rounding (no contraction left to the
+// compiler), so that the set-up tile masks and the kernels that read them see
+// the same offsets and the same in/out decisions.
+//
+// In-brick offset of local point p in FP32; the grid step is carried as two
+// FP32 words (hi + lo), so the offset has rounding errors only.
+__device__ __forceinline__ void point_offset(const GridDev& g, int p, float& fx, float& fy, float& fz) {
+    const int l2 = p % g.B[2], l1 = (p / g.B[2]) % g.B[1], l0 = p / (g.B[2] * g.B[1]);
+    const float f0 = (float)l0, f1 = (float)l1, f2 = (float)l2;
+    float v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float hi = __fmaf_rn(f2, g.step_hi[2][c], __fmaf_rn(f1, g.step_hi[1][c], __fmul_rn(f0, g.step_hi[0][c])));
+        const float lo = __fmaf_rn(f2, g.step_lo[2][c], __fmaf_rn(f1, g.step_lo[1][c], __fmul_rn(f0, g.step_lo[0][c])));
+        v[c] = __fadd_rn(hi, lo);
+    }
+    fx = v[0]; fy = v[1]; fz = v[2];
+}
+
+// (origin of brick (b0, b1, b2)) - (atom image position) in FP64, split into two FP32 words.
+__device__ __forceinline__ void brick_atom_offset(const GridDev& g, int b0, int b1, int b2, const ExtAtom& X,
+                                                  float c_hi[3], float c_lo[3]) {
+    const double s0 = (double)(b0 * g.B[0]), s1 = (double)(b1 * g.B[1]), s2 = (double)(b2 * g.B[2]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const double o = __dadd_rn(__dadd_rn(__dmul_rn(s0, g.step[0][q]), __dmul_rn(s1, g.step[1][q])), __dmul_rn(s2, g.step[2][q]));
+        const double c = __dsub_rn(o, X.p[q]);
+        c_hi[q] = __double2float_rn(c);
+        c_lo[q] = __double2float_rn(__dsub_rn(c, (double)c_hi[q]));
+    }
+}
+
+// |point - atom image| < rc for the point at in-brick offset f (FP32).
+__device__ __forceinline__ bool point_within(const float c_hi[3], const float c_lo[3], float fx, float fy, float fz,
+                                             float rc) {
+    const float dx = __fadd_rn(__fadd_rn(c_hi[0], fx), c_lo[0]);
+    const float dy = __fadd_rn(__fadd_rn(c_hi[1], fy), c_lo[1]);
+    const float dz = __fadd_rn(__fadd_rn(c_hi[2], fz), c_lo[2]);
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < __fmul_rn(rc, rc);
 }
 
 }  // namespace gint

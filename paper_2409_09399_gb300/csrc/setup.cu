@@ -427,6 +427,48 @@ __global__ void k_brick_pairs(Problem P, int64_t n_bricks, const double* rc_sp, 
     }
 }
 
+// Tile masks (once per geometry): for work item w and 128-point tile mt of its
+// brick, bit a is set when brick image a lies within rc of a point of the tile
+// (points p < bpts, the test the tensor-core rho and force kernels need; same
+// helpers and roundings as those kernels).  One warp per (item, tile); a brick
+// with more images than bits gets an empty mask (the tensor-core forms reject
+// such handles).
+__global__ void k_tile_mask(Problem P, int n_mt, unsigned long long* mask) {
+    const int64_t id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (id >= (int64_t)P.n_work * n_mt) return;
+    const int w = (int)(id / n_mt), mt = (int)(id - (int64_t)w * n_mt);
+    const GridDev& g = P.g;
+    const int brick = P.work[w];
+    int b0, b1, b2;
+    brick_coords(g, brick, b0, b1, b2);
+    const int64_t s0 = P.brick_start[brick];
+    const int na = (int)(P.brick_start[brick + 1] - s0);
+    unsigned long long m = 0ull;
+    if (na <= 64) {
+        float fx[4], fy[4], fz[4];
+        bool pv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int p = mt * 128 + 32 * k + lane;
+            pv[k] = p < g.bpts;
+            fx[k] = fy[k] = fz[k] = 0.f;
+            if (pv[k]) point_offset(g, p, fx[k], fy[k], fz[k]);
+        }
+        for (int a = 0; a < na; ++a) {
+            const ExtAtom X = P.ext[P.brick_atoms[s0 + a]];
+            float c_hi[3], c_lo[3];
+            brick_atom_offset(g, b0, b1, b2, X, c_hi, c_lo);
+            const float rc = P.sp[X.species].rc_f;
+            bool in = false;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) in = in || (pv[k] && point_within(c_hi, c_lo, fx[k], fy[k], fz[k], rc));
+            if (__any_sync(0xffffffffu, in)) m |= 1ull << a;
+        }
+    }
+    if (lane == 0) mask[id] = m;
+}
+
 __global__ void k_brick_stats(Problem P, int64_t n_bricks, const double* rc_sp, int64_t* nonempty_flag,
                               int64_t* pairs, int* max_atoms, int* max_orb) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -831,6 +873,16 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
     GINT_CUDA_TRY(cudaMalloc(&h->d_empty, sizeof(int32_t) * std::max<int64_t>(1, h->n_empty)));
     k_compact<<<(unsigned)((nbk + 255) / 256), 256, 0, st>>>(nbk, d_flag, d_pos_ne, h->d_work, h->d_empty, nullptr);
     GINT_CUDA_TRY(cudaGetLastError());
+    {
+        const int n_mt = (h->grid.bpad + 127) / 128;
+        const int64_t n_masks = h->n_work * n_mt;
+        GINT_CUDA_TRY(cudaMalloc(&h->d_tile_mask, sizeof(unsigned long long) * std::max<int64_t>(1, n_masks)));
+        if (n_masks > 0) {
+            Problem P = h->problem();
+            k_tile_mask<<<(unsigned)((n_masks * 32 + 255) / 256), 256, 0, st>>>(P, n_mt, h->d_tile_mask);
+            GINT_CUDA_TRY(cudaGetLastError());
+        }
+    }
     int mx[2];
     unsigned long long npairs = 0;
     GINT_CUDA_TRY(cudaMemcpy(mx, d_max, sizeof(int) * 2, cudaMemcpyDeviceToHost));
@@ -859,7 +911,7 @@ static void free_handle(gint_handle* h) {
     cudaGetDevice(&prev);
     cudaSetDevice(h->device);
     void* ptrs[] = {h->d_sp, h->d_coef64, h->d_coef32, h->d_knot32, h->d_ext, h->d_blocks, h->d_offsets, h->d_row_start,
-                    h->d_mirror, h->d_brick_start, h->d_brick_atoms, h->d_work, h->d_pair_start, h->d_pairs, h->d_empty, h->d_err, h->d_red,
+                    h->d_mirror, h->d_brick_start, h->d_brick_atoms, h->d_work, h->d_pair_start, h->d_pairs, h->d_tile_mask, h->d_empty, h->d_err, h->d_red,
                     h->d_scratch, h->d_nw_atom, h->d_atom_sp, h->d_orb_off, h->d_facc, h->d_dt, h->d_dq, h->d_zero};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -85,7 +85,6 @@ template <bool kExact> struct Smem {
     float qd[kMaxCols];                  // exact form: G scale 2^(qa + qD) of each output column of the group
     SpeciesFast spf[kMaxSpecies];
     unsigned char act[kMaxAtoms];
-    unsigned long long active_mask;
     uint64_t full[2];    // producers wrote A of buffer b (256 arrivals)
     uint64_t empty[2];   // MMAs reading buffer b completed (tcgen05.commit)
     uint64_t bfull[2];   // bulk copies of B into buffer b completed
@@ -157,17 +156,6 @@ __device__ __forceinline__ int warp_sum16_index(int lane) {
     return (((lane >> 4) & 1) << 3) | (((lane >> 3) & 1) << 2) | (((lane >> 2) & 1) << 1) | ((lane >> 1) & 1);
 }
 
-__device__ __forceinline__ void point_offset(const GridDev& g, int p, float& fx, float& fy, float& fz) {
-    // step = hi + lo (FP32 words): the offset carries rounding errors only, no scale error of the step
-    const int l2 = p % g.B[2], l1 = (p / g.B[2]) % g.B[1], l0 = p / (g.B[2] * g.B[1]);
-    const float f0 = (float)l0, f1 = (float)l1, f2 = (float)l2;
-    fx = (f0 * g.step_hi[0][0] + f1 * g.step_hi[1][0] + f2 * g.step_hi[2][0]) +
-         (f0 * g.step_lo[0][0] + f1 * g.step_lo[1][0] + f2 * g.step_lo[2][0]);
-    fy = (f0 * g.step_hi[0][1] + f1 * g.step_hi[1][1] + f2 * g.step_hi[2][1]) +
-         (f0 * g.step_lo[0][1] + f1 * g.step_lo[1][1] + f2 * g.step_lo[2][1]);
-    fz = (f0 * g.step_hi[0][2] + f1 * g.step_hi[1][2] + f2 * g.step_hi[2][2]) +
-         (f0 * g.step_lo[0][2] + f1 * g.step_lo[1][2] + f2 * g.step_lo[2][2]);
-}
 }  // namespace
 
 // Pre-format D: every block b as a 16 x 16 tile (zero padded) of hi and lo
@@ -310,17 +298,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
         brick_coords(g, brick, b0, b1, b2);
         const int64_t s0 = P.brick_start[brick];
         const int na = (int)(P.brick_start[brick + 1] - s0);
-        const double ox = b0 * g.B[0] * g.step[0][0] + b1 * g.B[1] * g.step[1][0] + b2 * g.B[2] * g.step[2][0];
-        const double oy = b0 * g.B[0] * g.step[0][1] + b1 * g.B[1] * g.step[1][1] + b2 * g.B[2] * g.step[2][1];
-        const double oz = b0 * g.B[0] * g.step[0][2] + b1 * g.B[1] * g.step[1][2] + b2 * g.B[2] * g.step[2][2];
         for (int i = tid; i < na; i += kThreads) {
             const ExtAtom X = P.ext[P.brick_atoms[s0 + i]];
             Atom& a = S.at[i];
-            const double c[3] = {ox - X.p[0], oy - X.p[1], oz - X.p[2]};
-            for (int q = 0; q < 3; ++q) {
-                a.c_hi[q] = (float)c[q];
-                a.c_lo[q] = (float)(c[q] - (double)a.c_hi[q]);
-            }
+            brick_atom_offset(g, b0, b1, b2, X, a.c_hi, a.c_lo);  // as in the set-up tile masks
             a.I = X.atom;
             a.sp = X.species;
             a.nw = P.sp[X.species].n_orb;
@@ -349,29 +330,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
 
         const int n_mtiles = (g.bpad + 127) / 128;
         for (int mt = 0; mt < n_mtiles && !S.abort; ++mt) {
-            // ---- active atom images of this M-tile
-            if (tid == 0) S.active_mask = 0ull;
-            __syncthreads();
-            if (tid < 128) {
-                const int p = mt * 128 + tid;
-                float fx = 0.f, fy = 0.f, fz = 0.f;
-                const bool pv = p < g.bpts;
-                if (pv) point_offset(g, p, fx, fy, fz);
-                for (int a = 0; a < na; ++a) {
-                    const Atom& X = S.at[a];
-                    const float dx = (X.c_hi[0] + fx) + X.c_lo[0];
-                    const float dy = (X.c_hi[1] + fy) + X.c_lo[1];
-                    const float dz = (X.c_hi[2] + fz) + X.c_lo[2];
-                    const float rc = P.sp[X.sp].rc_f;
-                    const bool in = pv && (dx * dx + dy * dy + dz * dz < rc * rc);
-                    if (__ballot_sync(0xffffffffu, in) && lane == 0) atomicOr(&S.active_mask, 1ull << a);
-                }
-            }
-            __syncthreads();
+            // ---- active atom images of this M-tile (images within rc of a point of the tile;
+            //      tested once per geometry at set-up, k_tile_mask)
             if (tid == 0) {
+                const unsigned long long m = __ldg(P.tile_mask + (int64_t)wl * n_mtiles + mt);
                 int n = 0;
                 for (int a = 0; a < na; ++a)
-                    if (S.active_mask >> a & 1ull) S.act[n++] = (unsigned char)a;
+                    if (m >> a & 1ull) S.act[n++] = (unsigned char)a;
                 S.nact = n;
             }
             __syncthreads();
