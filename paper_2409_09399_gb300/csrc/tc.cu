@@ -319,19 +319,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
             int e = 0;
             if (m > 0.f) frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
             S.scale_inv = ldexpf(1.f, e);
-            int off = 0;
+            int off = 0;  // first row of each image (the row tables are filled by all threads below)
             for (int i = 0; i < na; ++i) {
                 S.at[i].off = off;
-                const SpeciesFast& sf = S.spf[S.at[i].sp];
-                const SpeciesDev& sd = P.sp[S.at[i].sp];
-                for (int o = 0; o < S.at[i].nw; ++o) {
-                    S.row_atom[off + o] = (unsigned char)i;
-                    S.row_mu[off + o] = (unsigned char)o;
-                    if (kExact) {
-                        S.row_s[off + o] = (A.norm_after ? 1.0 : ylm_norm(sd.orb_l[o], sd.orb_m[o])) * (double)exp2i(sf.qeu[o]);
-                        S.row_f[off + o] = exp2i(sf.qeu[o]);
-                    }
-                }
                 off += S.at[i].nw;
             }
             // row tiles of 128; tile i accumulates columns [128 i, ncol), cut into segments
@@ -363,6 +353,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
         const float wscale = 1.f / S.scale_inv;
         for (int p = tid; p < g.bpad; p += kTcThreads) S.pt[p].w *= wscale;
         const int nrow = S.nrow, npass = S.npass;
+        // row tables: image and orbital of every row; exact form: the row's quantum 2^qeu (FP32)
+        // and, in FP64, times the harmonic normalisation unless k_norm_h applies it afterwards
+        for (int e = tid; e < na * kMaxNw; e += kTcThreads) {
+            const int i = e / kMaxNw, o = e - i * kMaxNw;
+            if (o >= S.at[i].nw) continue;
+            const int r = S.at[i].off + o;
+            S.row_atom[r] = (unsigned char)i;
+            S.row_mu[r] = (unsigned char)o;
+            if (kExact) {
+                const SpeciesFast& sf = S.spf[S.at[i].sp];
+                const SpeciesDev& sd = P.sp[S.at[i].sp];
+                S.row_s[r] = (A.norm_after ? 1.0 : ylm_norm(sd.orb_l[o], sd.orb_m[o])) * (double)exp2i(sf.qeu[o]);
+                S.row_f[r] = exp2i(sf.qeu[o]);
+            }
+        }
         // pair table of the brick (built once per geometry): block (I_a1, I_a2, t_a2 - t_a1), a1 <= a2
         {
             const int32_t* pt = P.pairs + P.pair_start[brick];
