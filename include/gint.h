@@ -124,7 +124,13 @@ void gint_destroy(gint_handle* h);
 gint_status gint_pattern(const gint_handle* h, int64_t* n_blocks, int64_t* n_values,
                          const int32_t** blocks, const int64_t** offsets);
 
-/* Select the arithmetic of later calls (gint_precision). */
+/* Select the arithmetic of later calls (gint_precision).  Host only: it sets
+ * a field of the handle and touches no device memory, so a caller may give
+ * each call its own form (every per-form table, such as the tensor-core copy
+ * of D, is made inside the call that uses it).  Calls already enqueued keep
+ * the form they were enqueued with.  GINT_ERR_INVALID_ARG for an unknown
+ * value; whether the handle's bricks suit a tensor-core form is reported by
+ * gint_check and by the compute calls. */
 gint_status gint_set_precision(gint_handle* h, int precision);
 
 /* H^V (Eq. 2).  V: device [n1][n2][n3] float64.  H: device, n_values float64
