@@ -579,17 +579,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                         tc::tmem_ld16(ta, v);
                         if (kExact) tc::tmem_ld16(ta + 256, v1);
                         if (!rvalid) continue;
+                        // the block of (a1, a2) and its size change only where a2 does (about twice
+                        // in 16 columns): looked up once per image
+                        int a2c = -1, blk = -1, nw2 = 0;
+                        int64_t off = 0;
 #pragma unroll
                         for (int jj = 0; jj < 16; ++jj) {
                             const int col = cs0 + 16 * gq + jj;
                             if (col >= nrow) continue;
                             const int a2 = S.row_atom[col];
-                            if (a1 > a2) continue;
-                            const int blk = S.pairblk[pair_index(a1, a2)];
-                            if (blk < 0) continue;
-                            const int64_t off = __ldg(P.offsets + blk);
+                            if (a2 != a2c) {
+                                a2c = a2;
+                                blk = a1 <= a2 ? S.pairblk[pair_index(a1, a2)] : -1;
+                                off = blk >= 0 ? __ldg(P.offsets + blk) : 0;
+                                nw2 = S.at[a2].nw;
+                            }
+                            if (blk < 0) continue;  // a1 > a2, or no block
                             const int nu = S.row_mu[col];
-                            const int nw2 = S.at[a2].nw;
                             if (a1 == a2 && r > col) continue;  // same image: symmetric block, keep r <= col
                             auto emit = [&](double x) {
                                 atomicAdd(H + off + mu * nw2 + nu, x);
@@ -597,18 +603,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                             };
                             // Three-product form: power-of-two scale (exact), widened to FP64 by bit
                             // arithmetic (no FP64 pipe).  Exact form with norm_after: the factors are a
-                            // power of two p2; the two accumulators are added with an error-free FP32
-                            // two-sum, scaled exactly, and both parts are added to H.  Exact form
-                            // accumulating into H: FP64 row and column factors (normalisation x quantum).
+                            // power of two p2; both accumulators are scaled exactly, widened by bit
+                            // arithmetic and added in FP64 (one DADD, one atomic; two FP32 values whose
+                            // exponents differ by at most 28 add exactly in FP64, else the sum rounds at
+                            // 2^-53 of the larger).  Exact form accumulating into H: FP64 row and column
+                            // factors (normalisation x quantum).
                             if (!kExact) {
                                 emit(f2d_exact(v[jj] * sinv));
                             } else if (A.norm_after) {
                                 const float p2 = qrf * S.row_f[col];
-                                const float a = v[jj], b = v1[jj];
-                                const float sm = a + b, bb = sm - a;
-                                const float er = (a - (sm - bb)) + (b - bb);
-                                emit(f2d_exact(sm * p2));
-                                if (er != 0.f) emit(f2d_exact(er * p2));
+                                emit(f2d_exact(v[jj] * p2) + f2d_exact(v1[jj] * p2));
                             } else {
                                 emit(((double)v[jj] + (double)v1[jj]) * (qr * S.row_s[col]));
                             }

@@ -332,12 +332,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
         for (int mt = 0; mt < n_mtiles && !S.abort; ++mt) {
             // ---- active atom images of this M-tile (images within rc of a point of the tile;
             //      tested once per geometry at set-up, k_tile_mask)
-            if (tid == 0) {
-                const unsigned long long m = __ldg(P.tile_mask + (int64_t)wl * n_mtiles + mt);
-                int n = 0;
-                for (int a = 0; a < na; ++a)
-                    if (m >> a & 1ull) S.act[n++] = (unsigned char)a;
-                S.nact = n;
+            if (warp == 0) {
+                const unsigned long long m = __ldg(P.tile_mask + (int64_t)wl * n_mtiles + mt);  // bits < na only
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int a = lane + 32 * h2;
+                    if (m >> a & 1ull) S.act[__popcll(m & ((1ull << a) - 1ull))] = (unsigned char)a;
+                }
+                if (lane == 0) S.nact = __popcll(m);
             }
             __syncthreads();
             const int nact = S.nact;
