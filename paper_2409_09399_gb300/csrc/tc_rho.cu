@@ -4,16 +4,21 @@
 // Both need, at every point p of a brick, G_p = Psi_p D_b (Psi_p: orbital
 // values at p over the brick's atom images, D_b the density-matrix blocks of
 // those images).  Per 128-point M-tile of a brick:
-//   * the tile's active atom images (non-zero somewhere in the tile) are
-//     listed; their orbitals are packed densely as the N dimension
-//     (<= 512 TMEM columns);
+//   * the tile's active atom images (within the cutoff of a point of the
+//     tile; a bit mask per (brick, tile) made once per geometry at set-up)
+//     give the N dimension: one 16-column slot per image (<= 512 TMEM
+//     columns; 256 in the exact form, more images take further column
+//     groups);
 //   * the K dimension runs over active atom images, one MMA K-step (16) per
 //     image (nw <= 16 orbitals, zero padded), two images per synchronisation:
-//     A = Psi restricted to that image (128 points x 16), B = the image's D
-//     blocks against every active
-//     image, copied row by row from a per-call pre-formatted copy of D
-//     (every pattern block as a 16 x 16 tile of hi/lo 16-bit pieces in
-//     K-major core-matrix order), so a B row is two 16-byte copies per piece;
+//     A = Psi restricted to that image (128 points x 16, MN-major), B = the
+//     image's D blocks against every image of the group, taken from a
+//     per-call pre-formatted copy of D (every pattern block as a 16 x 16
+//     tile of 16-bit pieces in K-major core-matrix order, the pieces
+//     interleaved per 8-row group), so one slot of B is one bulk copy;
+//   * three warp roles hand buffers over with mbarriers: eight warps
+//     evaluate A, one warp issues the bulk copies of B, one thread issues
+//     the MMAs (which never waits for earlier MMAs to complete);
 //   * G accumulates in TMEM (lane = point), three products per step
 //     (hi*hi + hi*lo + lo*hi);
 //   * exact form (fp16x4): both operands in fixed point, x / q = n + l1 + l2
@@ -158,9 +163,10 @@ __device__ __forceinline__ int warp_sum16_index(int lane) {
 
 }  // namespace
 
-// Pre-format D: every block b as a 16 x 16 tile (zero padded) of hi and lo
-// 16-bit pieces in K-major core-matrix order, values of block b taken from its
-// canonical block (transposed when b is not canonical).  One warp per block.
+// Pre-format D: every block b as a 16 x 16 tile (zero padded) of its 16-bit
+// pieces (hi, lo; exact form n, l1, l2) in K-major core-matrix order (dt_off),
+// values of block b taken from its canonical block (transposed when b is not
+// canonical).  One warp per block.
 // Largest |D| of every (atom I, orbital row i) over the blocks (I, J, T), as
 // FP32 bits (non-negative floats order like their bit patterns).
 __global__ void k_dmax(Problem P, const int32_t* mirror, const int* nw_atom, int64_t n_blocks, const double* D,
