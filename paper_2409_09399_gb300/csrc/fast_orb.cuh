@@ -95,9 +95,15 @@ __device__ __forceinline__ bool orbitals_fast(const SpeciesFast& s, const float2
     const float t1 = 1.f - t, tt = t * t;
     const float h00 = (1.f + 2.f * t) * t1 * t1, h10 = t * t1 * t1, h01 = tt * (3.f - 2.f * t), h11 = tt * (t - 1.f);
     const float g00 = 6.f * t * (t - 1.f), g10 = t1 * (1.f - 3.f * t), g11 = t * (3.f * t - 2.f);
-    const float2* kn = knot + s.knot2 + k * s.n_radial;
-    for (int j = 0; j < s.n_radial; ++j) {
-        const float2 y0 = ld_knot(kn + j), y1 = ld_knot(kn + s.n_radial + j);  // (R, dr R') at knots k, k + 1
+    const int nr = s.n_radial;
+    const float2* kn = knot + s.knot2 + k * nr;
+    // (R, dr R') at knots k, k + 1; those of radial function j + 1 are loaded before the
+    // values of j are formed, so their latency overlaps that work
+    float2 y0n = make_float2(0.f, 0.f), y1n = y0n;
+    if (nr > 0) { y0n = ld_knot(kn); y1n = ld_knot(kn + nr); }
+    for (int j = 0; j < nr; ++j) {
+        const float2 y0 = y0n, y1 = y1n;
+        if (j + 1 < nr) { y0n = ld_knot(kn + j + 1); y1n = ld_knot(kn + nr + j + 1); }
         const int l = s.rad_l[j];
         const int o = s.orb_base[j];
         float R = y0.x * h00 + y1.x * h01 + y0.y * h10 + y1.y * h11;
@@ -195,11 +201,19 @@ __device__ __forceinline__ bool orbitals_fast2(const SpeciesFast& s, const float
     const float sa = 1.f - ta, qa2 = ta * ta, sb = 1.f - tb, qb2 = tb * tb;
     const float a00 = (1.f + 2.f * ta) * sa * sa, a10 = ta * sa * sa, a01 = qa2 * (3.f - 2.f * ta), a11 = qa2 * (ta - 1.f);
     const float b00 = (1.f + 2.f * tb) * sb * sb, b10 = tb * sb * sb, b01 = qb2 * (3.f - 2.f * tb), b11 = qb2 * (tb - 1.f);
-    const float2* kna = knot + s.knot2 + ka * s.n_radial;
-    const float2* knb = knot + s.knot2 + kb * s.n_radial;
-    for (int j = 0; j < s.n_radial; ++j) {
-        const float2 pa = ld_knot(kna + j), qa = ld_knot(kna + s.n_radial + j);
-        const float2 pb = ld_knot(knb + j), qb = ld_knot(knb + s.n_radial + j);
+    const int nr = s.n_radial;
+    const float2* kna = knot + s.knot2 + ka * nr;
+    const float2* knb = knot + s.knot2 + kb * nr;
+    // the knots of radial function j + 1 are loaded before the values of j are formed and
+    // stored, so their latency overlaps that work
+    float2 pa = make_float2(0.f, 0.f), qa = pa, pb = pa, qb = pa;
+    if (nr > 0) { pa = ld_knot(kna); qa = ld_knot(kna + nr); pb = ld_knot(knb); qb = ld_knot(knb + nr); }
+    for (int j = 0; j < nr; ++j) {
+        float2 pa1 = pa, qa1 = qa, pb1 = pb, qb1 = qb;
+        if (j + 1 < nr) {
+            pa1 = ld_knot(kna + j + 1); qa1 = ld_knot(kna + nr + j + 1);
+            pb1 = ld_knot(knb + j + 1); qb1 = ld_knot(knb + nr + j + 1);
+        }
         const int l = s.rad_l[j];
         const int o = s.orb_base[j];
         float ua = (pa.x * a00 + qa.x * a01 + pa.y * a10 + qa.y * a11) * ma;
@@ -221,15 +235,16 @@ __device__ __forceinline__ bool orbitals_fast2(const SpeciesFast& s, const float
             put2(o + 4, ua * k2c * (ax * ax - ay * ay), ub * k2c * (bx * bx - by * by));
         } else {
             const float xxa = ax * ax, yya = ay * ay, zza = az * az, xxb = bx * bx, yyb = by * by, zzb = bz * bz;
-            const float qa = 4.f * zza - xxa - yya, qb = 4.f * zzb - xxb - yyb;
+            const float wa = 4.f * zza - xxa - yya, wb = 4.f * zzb - xxb - yyb;
             put2(o + 0, ua * k3a * ay * (3.f * xxa - yya), ub * k3a * by * (3.f * xxb - yyb));
             put2(o + 1, ua * k3b * ax * ay * az, ub * k3b * bx * by * bz);
-            put2(o + 2, ua * k3c * ay * qa, ub * k3c * by * qb);
+            put2(o + 2, ua * k3c * ay * wa, ub * k3c * by * wb);
             put2(o + 3, ua * k3d * az * (2.f * zza - 3.f * xxa - 3.f * yya), ub * k3d * bz * (2.f * zzb - 3.f * xxb - 3.f * yyb));
-            put2(o + 4, ua * k3c * ax * qa, ub * k3c * bx * qb);
+            put2(o + 4, ua * k3c * ax * wa, ub * k3c * bx * wb);
             put2(o + 5, ua * k3e * az * (xxa - yya), ub * k3e * bz * (xxb - yyb));
             put2(o + 6, ua * k3a * ax * (xxa - 3.f * yya), ub * k3a * bx * (xxb - 3.f * yyb));
         }
+        pa = pa1; qa = qa1; pb = pb1; qb = qb1;
     }
     return true;
 }
