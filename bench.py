@@ -106,6 +106,21 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws, device):
+    """x of this rank -> the largest x over the ranks (x itself for one rank)."""
+    if ws == 1:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, steps, ws, t_max_ms):
+    """Units that all ranks processed in the timed steps, per second of the slowest rank."""
+    return units_per_rank * steps * ws / (t_max_ms / 1e3)
+
+
 # ----------------------------------------------------------------- oracle arm
 def oracle_inputs(system):
     """The oracle and its inputs for `system` (input generation and set-up, never timed)."""
@@ -312,22 +327,17 @@ def run_ours(args):
             step(recs[k])
         end.record(stream)
         torch.cuda.synchronize()
+    barrier()
     g.sync()
     total_ms = t0.elapsed_time(end)
     parts = np.zeros(3)
     for k in range(args.steps):
         r = recs[k]
-        nxt = recs[k + 1][0] if k + 1 < args.steps else end
         parts += [r[0].elapsed_time(r[1]), r[1].elapsed_time(r[2]), r[2].elapsed_time(r[3])]
-        _ = nxt
     parts /= args.steps
-    t_max = total_ms
-    if ws > 1:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(total_ms, ws, dev)
     ms_per_step = t_max / args.steps
-    value = ng * args.steps * ws / (t_max / 1e3)
+    value = whole_job_rate(ng, args.steps, ws, t_max)
 
     H_mixed, rho_mixed, F_mixed = H.clone(), rho.clone(), F.clone()
 
@@ -394,10 +404,10 @@ def run_ours(args):
         b.record(stream)
         torch.cuda.synchronize()
         g.sync()
-        ms_e2e = a.elapsed_time(b) / args.e2e_steps
+        ms_e2e = max_over_ranks(a.elapsed_time(b) / args.e2e_steps, ws, dev)
         h2d = (Vh.numel() + Dh.numel()) * 8
         d2h = (Hh.numel() + rhoh.numel() + Fh.numel() + sigh.numel() + Eh.numel()) * 8
-        e2e = {"value": ng * ws / (ms_e2e / 1e3), "unit": "grid_points/s", "h2d_bytes_per_step": h2d,
+        e2e = {"value": whole_job_rate(ng, 1, ws, ms_e2e), "unit": "grid_points/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
         del Vh, Dh, Hh, rhoh, Vd, Dd
 
