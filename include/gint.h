@@ -69,14 +69,17 @@ typedef enum {
     GINT_FP64 = 0,
     GINT_FP32 = 1,     /* FP32 orbital values and FP32 SIMT contractions */
     GINT_TF32 = 2,     /* reserved */
-    GINT_BF16X3 = 3,   /* H^V on the tensor cores: operands split x = hi + lo in bf16,
-                          products hi*hi + hi*lo + lo*hi, FP32 accumulation per brick */
+    GINT_BF16X3 = 3,   /* H^V, rho and force on the tensor cores: operands split
+                          x = hi + lo in bf16, products hi*hi + hi*lo + lo*hi, FP32
+                          accumulation per brick (H^V) or per 128-point tile (rho, force) */
     GINT_BF16X6 = 4,   /* reserved */
     GINT_FP16X3 = 5,   /* as GINT_BF16X3 with fp16 pieces (22-bit products) */
-    GINT_FP16X4 = 6    /* tensor cores, exact leading term: each operand value x of orbital o
-                          is x / 2^qe_o = n + l, n an integer of <= 8 bits (exact in fp16),
-                          l in fp16; the products n*n accumulate exactly in FP32, the cross
-                          terms n*l + l*n + l*l in a second FP32 accumulator */
+    GINT_FP16X4 = 6    /* tensor cores, exact leading term: each operand value x is written
+                          x / q = n + l1 + l2 with q a power of two (per orbital for the
+                          orbital values, per (atom, orbital row) for D), n an integer of
+                          <= 8 bits (exact in fp16) and l1, l2 fp16 pieces of the rest;
+                          the products n*n accumulate exactly in FP32, the cross terms
+                          n*l1 + l1*n + l1*l1 + n*l2 + l2*n in a second FP32 accumulator */
 } gint_precision;
 
 /* One tabulated radial function R(r): y[k] = R(k*dr), dy[k] = R'(k*dr),
