@@ -242,7 +242,10 @@ gint_status gint_get_info(const gint_handle* h, gint_info* info);
  * synchronises the device.  Outputs are host pointers. */
 gint_status gint_work_stats(gint_handle* h, int64_t* sum_orbitals, int64_t* sum_orbitals_sq);
 
-/* Message of the last failed call on this host thread ("" if none). */
+/* Message of the last failed call on this host thread.  gint_setup, the
+ * compute calls (gint_vlocal, gint_rho, gint_force_stress, gint_vlocal_static,
+ * gint_fold_k), gint_check and gint_batch_create/run clear it when they start,
+ * so after one of them succeeds it is "". */
 const char* gint_last_error(void);
 
 #ifdef __cplusplus

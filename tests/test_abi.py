@@ -50,3 +50,24 @@ def test_host_validation_without_gpu():
     assert L.gint_force_stress(None, None, None, None, None, None, None, None) == 1
     assert L.gint_set_precision(None, 0) == 1
     L.gint_destroy(None)  # no-op
+
+
+def test_host_validation_of_the_other_entry_points():
+    """NULL handles and empty batches are refused by status on the host (no device touched)."""
+    from paper_2409_09399_gb300 import gint
+    L = gint.load()
+    i64 = ctypes.c_int64
+    assert L.gint_check(None) == 1
+    assert L.gint_vlocal_static(None, None, None, None) == 1
+    k = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    assert L.gint_fold_k(None, None, ctypes.byref(k), None, 0, None) == 1
+    assert b"gint_fold_k" in L.gint_last_error()
+    out = ctypes.c_void_p()
+    assert L.gint_batch_create(0, None, ctypes.byref(out)) == 1 and out.value is None
+    assert L.gint_batch_run(None, None, None, None, None, None, None, None, None) == 1
+    L.gint_batch_destroy(None)  # no-op
+    assert L.gint_sync(None, None) == 1
+    assert L.gint_get_info(None, None) == 1
+    a, b = i64(), i64()
+    assert L.gint_work_stats(None, ctypes.byref(a), ctypes.byref(b)) == 1
+    assert L.gint_pattern(None, None, None, None, None) == 1
