@@ -69,12 +69,17 @@ def autotune_brick(systems: Sequence, precision="fp16x3", candidates=CANDIDATE_B
                 table[brick][i] = _time_calls(g, V, D)
             finally:
                 g.close()
+    return rank_shapes(table), table
+
+
+def rank_shapes(table: Dict[tuple, Dict[int, Optional[float]]]) -> List[tuple]:
+    """Shapes from fastest to slowest: first by how many sampled systems cannot take the
+    shape (None), then by the summed time on the systems that can (ties keep table order)."""
     def key(b):
         t = table[b]
         missing = sum(v is None for v in t.values())
         return (missing, sum(v for v in t.values() if v is not None))
-    ranking = sorted(table, key=key)
-    return ranking, table
+    return sorted(table, key=key)
 
 
 def brick_for(system, precision, ranking) -> Tuple[int, int, int]:
