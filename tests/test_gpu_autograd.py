@@ -102,4 +102,4 @@ def test_mixed_gradient_against_oracle_tbg15(cuda):
                        atoms=atoms)
     err = np.max(np.abs(-pos.grad.numpy()[atoms] - F_ref))
     print(f"TBG m=15 fp16x3 dE/dR vs oracle: {err:.2e} (max |F| {np.abs(F_ref).max():.2f})")
-    assert err < 5e-5
+    assert err < 1e-5  # the stated force target (Ha/bohr)
