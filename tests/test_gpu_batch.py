@@ -94,7 +94,8 @@ def test_batch_mixed_vs_single_and_fp64(cuda):
         worst["F"] = max(worst["F"], eF)
         g64.close()
     print("worst per-cell error vs FP64:", worst)
-    assert worst["H"] < 5e-5 and worst["rho"] < 1e-4 and worst["F"] < 1e-4
+    # fp16x3 meets the force target (F <= 1e-5 Ha/bohr); H and rho carry its accumulation bias
+    assert worst["H"] < 5e-5 and worst["rho"] < 1e-4 and worst["F"] < 1e-5
 
 
 def test_batch_fp64_vs_oracle(cuda):
@@ -123,3 +124,61 @@ def test_batch_fp64_vs_oracle(cuda):
         eF = np.max(np.abs(F[i].cpu().numpy() - F_ref)) / max(1.0, np.max(np.abs(F_ref)))
         print(f"fp64 cell {s.name}: H {eH:.2e} rho {eR:.2e} F {eF:.2e}")
         assert eH < 1e-11 and eR < 1e-11 and eF < 1e-10
+
+
+# per-result bounds of the queue path against the oracle.  These cells have coarse grids
+# (0.47-0.63 bohr against the TBG workloads' 0.157), where the exact form's H error is set by
+# the FP32 orbital values (|r| in FP32, about 3e-7 relative per value) and averages out over
+# fewer points: bounded by 5e-7 x max(1, max|H|) as in the other coarse-grid tests.
+QUEUE_TOL = {"fp16x4": {"H": 5e-7, "rho": 1e-6, "F": 1e-5, "sigma": 1e-5},
+             "fp16x3": {"H": 5e-5, "rho": 1e-4, "F": 1e-5, "sigma": 1e-4}}
+QUEUE_CELLS = (5, 21, 3, 15, 7)  # two dense cells (0.09 atoms per cubic angstrom), 20-81 atoms, grids 24^3-39^3
+_oracle_cache = {}
+
+
+def _oracle_cell(i):
+    if i not in _oracle_cache:
+        s = synth.random_cell(i)
+        o = oracle.Oracle(s)
+        V = synth.v_grid(s.grid, synth.plane_wave_params()).numpy()
+        D = o.d_fill()
+        F, W = o.force(V, D)
+        _oracle_cache[i] = (s, o, V, D, o.vlocal(V), o.rho(D), F, W, o.energy(V, D))
+    return _oracle_cache[i]
+
+
+@pytest.mark.parametrize("precision", ["fp16x4", "fp16x3"])
+def test_batch_queue_vs_oracle(precision, cuda):
+    """The multi-cell persistent queue (one launch per call over every cell's bricks) against the
+    oracle, element by element, for uneven C/H/O cells."""
+    import torch
+    from paper_2409_09399_gb300.batch import GintBatch, brick_for
+    cases = [_oracle_cell(i) for i in QUEUE_CELLS]
+    systems = [c[0] for c in cases]
+    order = ((4, 4, 8), (4, 4, 4), (2, 4, 4), (2, 2, 4), (2, 2, 2))
+    bricks = [brick_for(s, precision, order) for s in systems]
+    b = GintBatch(systems, precision=precision, brick=bricks)
+    # every cell takes the same tensor-core form and passes its limits: the batch runs the
+    # (cell, brick) queue, not per-cell calls
+    assert all(h.supported() for h in b.handles)
+    Vs = [torch.from_numpy(c[2]).cuda() for c in cases]
+    Ds = [torch.from_numpy(c[3]).cuda() for c in cases]
+    for h, c in zip(b.handles, cases):
+        blocks, offsets = h.pattern()
+        assert np.array_equal(blocks, c[1].blocks) and np.array_equal(offsets, c[1].offsets)
+    H, rho, F, sig, E = _run_batch(b, systems, Vs, Ds)
+    tol = QUEUE_TOL[precision]
+    for i, (s, o, V, D, H_ref, r_ref, F_ref, W_ref, E_ref) in enumerate(cases):
+        eH = float(np.max(np.abs(H[i].cpu().numpy() - H_ref)))
+        eR = float(np.max(np.abs(rho[i].cpu().numpy() - r_ref)) / np.max(np.abs(r_ref)))
+        eF = float(np.max(np.abs(F[i].cpu().numpy() - F_ref)))
+        s_ref = -W_ref.sum(0) / o.omega
+        eS = float(np.max(np.abs(sig[i].cpu().numpy() - s_ref)))
+        eE = abs(float(E[i]) - E_ref) / abs(E_ref)
+        print(f"{precision} cell {QUEUE_CELLS[i]} ({s.n_atoms} atoms, grid {s.grid[0]}^3, brick {bricks[i]}): "
+              f"H {eH:.2e} (max {np.abs(H_ref).max():.2f}) rho {eR:.2e} F {eF:.2e} sigma {eS:.2e} E {eE:.2e}")
+        assert eH < tol["H"] * max(1.0, float(np.max(np.abs(H_ref))))
+        assert eR < tol["rho"]
+        assert eF < tol["F"] * max(1.0, float(np.max(np.abs(F_ref))))
+        assert eS < tol["sigma"] * max(1.0, float(np.max(np.abs(s_ref))))
+        assert eE < tol["rho"]

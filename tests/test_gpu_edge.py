@@ -93,3 +93,109 @@ def test_zero_inputs(precision, cuda):
     g.sync()
     assert float(H.abs().max()) == 0.0 and float(F.abs().max()) == 0.0 and float(E.abs().max()) == 0.0
     assert float(rho.abs().max()) == 0.0 and float(F2.abs().max()) == 0.0 and float(E2.abs().max()) == 0.0
+
+
+# ------------------------------------------------ atoms exactly on grid points
+# At |d| = 0 every kernel takes the limits of the orbitals (phi = R(0) Y00 for l = 0 and 0
+# otherwise; grad phi = R'(0) grad S_1m for l = 1 and 0 otherwise), the same limits the
+# oracle's closed-form pins fix.
+
+def diamond_on_grid():
+    """Undisplaced diamond on a 20^3 grid: all 8 atoms sit on grid points (fractions 0, 1/4, 1/2, 3/4)."""
+    return synth.diamond(disp_ang=0.0, grid=(20, 20, 20))
+
+
+def _brick_for(s, precision, candidates=((8, 8, 8), (4, 4, 8), (4, 4, 4), (2, 4, 4), (2, 2, 4), (2, 2, 2))):
+    from paper_2409_09399_gb300 import gint
+    for b in candidates:
+        g = gint.from_system(s, precision=precision, brick=b)
+        if g.supported():
+            return g, b
+        g.close()
+    raise AssertionError(f"no brick shape accepted for {precision}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp16x4", "fp16x3"])
+def test_atoms_on_grid_points_diamond(precision, cuda):
+    import torch
+    s = diamond_on_grid()
+    frac = np.linalg.solve(s.cell.T, s.pos.T).T * np.array(s.grid)
+    assert np.allclose(frac, np.round(frac), atol=1e-12)  # every atom on a grid point
+    key = "diamond_on_grid"
+    if key not in _cache:
+        o = oracle.Oracle(s)
+        V = synth.v_grid(s.grid, synth.plane_wave_params()).numpy()
+        D = o.d_fill()
+        F, W = o.force(V, D)
+        _cache[key] = (o, V, D, o.vlocal(V), o.rho(D), F, W)
+    o, V, Dor, H_ref, rho_ref, F_ref, W_ref = _cache[key]
+    g, brick = _brick_for(s, precision)
+    blocks, offsets = g.pattern()
+    assert np.array_equal(blocks, o.blocks) and np.array_equal(offsets, o.offsets)
+    Vt = torch.from_numpy(V).cuda()
+    D = torch.from_numpy(Dor).cuda()
+    H = g.vlocal(Vt).cpu().numpy()
+    rho = g.rho(D).cpu().numpy()
+    F, sigma, vir, E = g.force_stress(Vt, D)
+    g.sync()
+    tH, tR, tF = TOL[precision]
+    eH = np.max(np.abs(H - H_ref))
+    eR = np.max(np.abs(rho - rho_ref)) / np.max(np.abs(rho_ref))
+    eF = np.max(np.abs(F.cpu().numpy() - F_ref))
+    sig_ref = -W_ref.sum(0) / o.omega
+    eS = np.max(np.abs(sigma.cpu().numpy() - sig_ref))
+    # the density at the atom sites (grid points holding an atom) on its own
+    sites = np.round(frac).astype(np.int64) % np.array(s.grid)
+    eSite = np.max(np.abs(rho[sites[:, 0], sites[:, 1], sites[:, 2]] - rho_ref[sites[:, 0], sites[:, 1], sites[:, 2]]))
+    print(f"diamond on grid {precision} brick {brick}: H {eH:.2e} rho {eR:.2e} (sites {eSite:.2e}) F {eF:.2e} "
+          f"sigma {eS:.2e}")
+    assert eH < tH * max(1.0, np.max(np.abs(H_ref))) and eR < tR and eF < tF * max(1.0, np.max(np.abs(F_ref)))
+    assert eSite < tR * np.max(np.abs(rho_ref))
+    assert eS < tF * max(1.0, np.max(np.abs(sig_ref)))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp16x4", "fp16x3"])
+def test_atom_on_grid_point_tbg(precision, cuda):
+    """TBG m=2 shifted so that atom 0 sits on grid point (0, 0, 0) (its layer then straddles the
+    cell boundary along a3): blocks of atom 0, rho around it and the forces of atom 0 and two
+    others against the oracle, in the benchmark's brick shape."""
+    import torch
+    from paper_2409_09399_gb300 import gint
+    s0 = synth.tbg(2)
+    s = synth.System("tbg2_on_grid", s0.cell, s0.pos - s0.pos[0], s0.species_index, s0.species, s0.grid)
+    key = "tbg2_on_grid"
+    if key not in _cache:
+        o = oracle.Oracle(s)
+        V = synth.v_grid(s.grid, synth.plane_wave_params()).numpy()
+        D = o.d_fill()
+        rows = np.nonzero(o.blocks[:, 0] == 0)[0]
+        rng = np.random.default_rng(5)
+        sel = np.concatenate([rows, rng.choice(len(o.blocks), 16, replace=False)])
+        Hs = o.vlocal_blocks(V, o.blocks[sel])
+        # every grid point within 2 grid steps of the origin (periodic), plus random points
+        near = np.array([(i, j, k) for i in range(-2, 3) for j in range(-2, 3) for k in range(-2, 3)])
+        idx = np.concatenate([near % np.array(s.grid), np.stack([rng.integers(0, n, 300) for n in s.grid], 1)])
+        rs = o.rho_points(D, idx)
+        atoms = np.array([0, 5, 40])
+        F, _ = o.force(V, D, atoms=atoms)
+        _cache[key] = (o, V, D, sel, Hs, idx, rs, atoms, F)
+    o, V, Dor, sel, Hs, idx, rs, atoms, F_ref = _cache[key]
+    g = gint.from_system(s, precision=precision, brick=(8, 8, 8))
+    assert g.supported()
+    blocks, offsets = g.pattern()
+    assert np.array_equal(blocks, o.blocks)
+    Vt = torch.from_numpy(V).cuda()
+    D = torch.from_numpy(Dor).cuda()
+    H = g.vlocal(Vt).cpu().numpy()
+    rho = g.rho(D).cpu().numpy()
+    F, _, _, _ = g.force_stress(Vt, D)
+    g.sync()
+    eH = max(float(np.max(np.abs(H[offsets[b]:offsets[b + 1]].reshape(r.shape) - r))) for b, r in zip(sel, Hs))
+    got = rho[idx[:, 0], idx[:, 1], idx[:, 2]]
+    eR = float(np.max(np.abs(got - rs)) / np.max(np.abs(rs)))
+    eF = float(np.max(np.abs(F.cpu().numpy()[atoms] - F_ref)))
+    print(f"TBG m=2 atom on grid {precision}: H {eH:.2e} rho {eR:.2e} (at the atom {abs(got[62] - rs[62]):.2e}) "
+          f"F {eF:.2e}")
+    tol = {"fp64": (1e-11, 1e-11, 1e-10), "fp16x4": (1e-7, 1e-6, 1e-5), "fp16x3": (5e-5, 1e-4, 1e-5)}[precision]
+    scaleH = 1.0 if precision != "fp64" else max(1.0, max(float(np.max(np.abs(r))) for r in Hs))
+    assert eH < tol[0] * scaleH and eR < tol[1] and eF < tol[2] * max(1.0, float(np.max(np.abs(F_ref))))

@@ -397,3 +397,142 @@ def test_supercell_consistency():
         D2[o2.offsets[b]:o2.offsets[b + 1]] = o.block(D, ub).reshape(-1)
     assert worst < 1e-13 * np.max(np.abs(H))
     assert abs(o2.energy(V2, D2) - 2 * E) < 1e-12 * abs(E)
+
+
+# --------------------------------------------- atom-centre limit (|d| -> 0)
+def _centre_closed_form(shells):
+    """phi(0) and grad phi(0) of r^l sum_k c_k exp(-a_k r^2) Y_lm, oracle orbital order.
+
+    phi = (sum_k c_k exp(-a_k r^2)) S_lm(d) with S_lm = r^l Y_lm a polynomial of
+    degree l, so at d = 0: phi = sum c / sqrt(4 pi) for l = 0 and 0 for l >= 1;
+    grad phi = sum c grad S_1m for l = 1 (the constant gradient of the linear
+    polynomial) and 0 for l = 0 (the Gaussian is flat at the centre) and l >= 2.
+    """
+    phi, grad = [], []
+    for l in range(4):
+        for (ll, al, co) in shells:
+            if ll != l:
+                continue
+            csum = float(sum(co))
+            for poly in solid_harmonic_polys(l):
+                g = np.zeros(3)
+                if l == 1:
+                    (i, j, k), v = next(iter(poly.items()))
+                    g[[i, j, k].index(1)] = csum * v
+                phi.append(csum * poly.get((0, 0, 0), 0.0))
+                grad.append(g)
+    return np.array(phi), np.array(grad)
+
+
+def test_orbitals_at_atom_centre_closed_form():
+    """At d = 0 the oracle returns the limits of Eq. 2's orbitals, not 0/0."""
+    sp = gaussian_species(SHELLS)
+    o = oracle.Oracle(system([[0, 0, 0]], np.eye(3) * 30, sp, (4, 4, 4)))
+    phi, g = o.eval_orbitals(0, np.zeros((1, 3)))
+    phi_ref, g_ref = _centre_closed_form(SHELLS)
+    assert np.all(np.isfinite(phi)) and np.all(np.isfinite(g))
+    # the Hermite table reproduces R(0) = y_0 and R'(0) = y'_0 exactly at the first knot
+    assert np.max(np.abs(phi[0] - phi_ref)) < 1e-14, (phi[0], phi_ref)
+    assert np.max(np.abs(g[0] - g_ref)) < 1e-14, (g[0], g_ref)
+    # the p orbitals (y, z, x order) carry the only non-zero gradients
+    assert np.count_nonzero(np.abs(g[0]).sum(1) > 0) == 3
+
+
+@pytest.mark.parametrize("basis", ["gauss", "C_DZP"])
+def test_orbitals_continuous_at_atom_centre(basis):
+    """phi and grad phi at |d| = 1e-7 and 1e-9 along several directions equal their values at d = 0."""
+    sp = gaussian_species(SHELLS) if basis == "gauss" else synth.make_species("C", "DZP")
+    o = oracle.Oracle(system([[0, 0, 0]], np.eye(3) * 30, sp, (4, 4, 4)))
+    p0, g0 = o.eval_orbitals(0, np.zeros((1, 3)))
+    rng = np.random.default_rng(11)
+    n = rng.normal(size=(12, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    for r in (1e-7, 1e-9):
+        p, g = o.eval_orbitals(0, n * r)
+        assert np.max(np.abs(p - p0)) < 1e-5, (r, np.max(np.abs(p - p0)))
+        assert np.max(np.abs(g - g0)) < 1e-5, (r, np.max(np.abs(g - g0)))
+    # and away from the limit branch the same values are approached smoothly (FD of phi at 1e-4)
+    h = 1e-5
+    for a in range(3):
+        e = np.zeros((1, 3)); e[0, a] = h
+        pp, _ = o.eval_orbitals(0, e)
+        pm, _ = o.eval_orbitals(0, -e)
+        assert np.max(np.abs((pp - pm) / (2 * h) - g0[:, :, a])) < 1e-4
+
+
+def test_density_and_force_with_atom_on_grid_point():
+    """An atom exactly on a grid point: rho there is finite and the force equals -dE/dR (Eq. 3, 4)."""
+    sp = synth.make_species("O", "SZP")
+    cell = np.eye(3) * 9.0
+    grid = (18, 18, 18)
+    pos = np.array([[0.0, 0.0, 0.0], [4.5, 3.0, 5.5]])  # atom 0 on grid point (0, 0, 0)
+    s = system(pos, cell, sp, grid)
+    o = oracle.Oracle(s)
+    V = synth.v_grid(s.grid, synth.plane_wave_params()).numpy()
+    D = o.d_fill()
+    rho0 = o.rho_points(D, [[0, 0, 0]])
+    assert np.isfinite(rho0).all()
+    F, _ = o.force(V, D, atoms=[0])
+    Dmap = {tuple(int(x) for x in k): o.block(D, b).copy() for b, k in enumerate(o.blocks)}
+
+    def energy_at(p):
+        op = oracle.Oracle(s, pos=p)
+        Dp = np.zeros(op.n_values)
+        for b, k in enumerate(op.blocks):
+            blk = Dmap.get(tuple(int(x) for x in k))
+            if blk is not None:
+                Dp[op.offsets[b]:op.offsets[b + 1]] = blk.reshape(-1)
+        return op.energy(V, Dp)
+
+    delta = 1e-4
+    scale = max(1e-3, np.max(np.abs(F)))
+    for a in range(3):
+        p1 = pos.copy(); p1[0, a] += delta
+        p0 = pos.copy(); p0[0, a] -= delta
+        fd = -(energy_at(p1) - energy_at(p0)) / (2 * delta)
+        assert abs(fd - F[0, a]) < 2e-6 * scale + 1e-9, (a, fd, F[0, a])
+
+
+# ----------------------------------------------------- pattern enumeration
+def brute_force_pattern(pos, cell, rc, tmax):
+    """All (I, J, t) with |R_J + t A - R_I| < rc_I + rc_J for |t_i| <= tmax, sorted (plain numpy)."""
+    rng_t = np.arange(-tmax, tmax + 1)
+    T = np.stack(np.meshgrid(rng_t, rng_t, rng_t, indexing="ij"), -1).reshape(-1, 3)
+    TA = T @ cell
+    rows = []
+    for I in range(len(pos)):
+        for J in range(len(pos)):
+            d = pos[J] + TA - pos[I]
+            keep = np.sqrt((d * d).sum(1)) < rc[I] + rc[J]
+            for t in T[keep]:
+                rows.append((I, J, int(t[0]), int(t[1]), int(t[2])))
+    rows.sort()
+    return np.array(rows, dtype=np.int64).reshape(-1, 5)
+
+
+def test_pattern_diamond_block_count():
+    """Diamond (8 C, rc = 7 bohr): 2,344 blocks, equal to a brute force over |t_i| <= 5 (Section 2.2 sparsity)."""
+    s = synth.diamond()
+    o = oracle.Oracle(s)
+    ref = brute_force_pattern(s.pos, s.cell, np.full(s.n_atoms, 7.0), 5)
+    assert len(ref) == 2344
+    assert np.array_equal(o.blocks, ref)
+    nw = s.nw()
+    assert o.offsets[-1] == int(np.sum(nw[ref[:, 0]] * nw[ref[:, 1]]))
+
+
+def test_pattern_hexagonal_two_species():
+    """A skewed hexagonal two-species cell with different cutoffs: the oracle's pattern equals the brute force."""
+    a = 8.3
+    cell = np.array([[a, 0, 0], [0.5 * a, 0.5 * math.sqrt(3) * a, 0], [0.7, -0.4, 12.0]])
+    sps = [synth.make_species("C", "DZP"), synth.make_species("H", "DZP", rc=5.5, taper_start=4.5)]
+    pos = np.array([[0.3, 0.2, 1.0], [4.1, 2.2, 6.5], [6.6, 5.0, 3.3], [1.7, 3.9, 9.8]])
+    spi = np.array([0, 1, 0, 1], np.int32)
+    s = system(pos, cell, sps, (16, 16, 24), spi=spi)
+    o = oracle.Oracle(s)
+    rc = np.array([sps[k].rc for k in spi])
+    ref = brute_force_pattern(pos, cell, rc, 6)
+    assert np.array_equal(o.blocks, ref)
+    # closed under (I, J, T) -> (J, I, -T)
+    keys = {tuple(r) for r in ref.tolist()}
+    assert all((J, I, -t1, -t2, -t3) in keys for (I, J, t1, t2, t3) in keys)
