@@ -248,6 +248,117 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------- our arm
+class EndToEnd:
+    """Steps through the public API with the inputs in pinned host memory: every step copies V
+    and D to the device, runs H^V, rho and force/stress, and copies H, rho, F, sigma and E back.
+
+    ``use(call)`` sets the handle's form for a call (or does nothing).  ``inline`` keeps the
+    copies in line with each step on the compute stream; ``overlapped`` hides them behind the
+    neighbouring steps' compute (uploads of step k + 1 and downloads of step k on two copy
+    streams, ordered by events, with two sets of device inputs and outputs)."""
+
+    def __init__(self, g, V, D, use, stream, dev):
+        import torch
+        self.g, self.use, self.stream, self.dev = g, use, stream, dev
+        self.Vh = V.cpu().pin_memory()
+        self.Dh = D.cpu().pin_memory()
+        n_at = g.n_atoms
+        f64 = torch.float64
+        self.Hh = torch.empty(g.n_values, dtype=f64).pin_memory()
+        self.rhoh = torch.empty(g.grid, dtype=f64).pin_memory()
+        self.Fh = torch.empty((n_at, 3), dtype=f64).pin_memory()
+        self.sigh = torch.empty((3, 3), dtype=f64).pin_memory()
+        self.Eh = torch.empty(1, dtype=f64).pin_memory()
+
+        def outs():
+            return (torch.empty(g.n_values, dtype=f64, device=dev), torch.empty(g.grid, dtype=f64, device=dev),
+                    torch.empty((n_at, 3), dtype=f64, device=dev), torch.empty((3, 3), dtype=f64, device=dev),
+                    torch.empty((n_at, 3, 3), dtype=f64, device=dev), torch.empty(1, dtype=f64, device=dev))
+        self.Vd = [torch.empty_like(V), None]
+        self.Dd = [torch.empty_like(D), None]
+        self.out = [outs(), None]
+        self._outs = outs
+        self.h2d_bytes = (self.Vh.numel() + self.Dh.numel()) * 8
+        self.d2h_bytes = (self.Hh.numel() + self.rhoh.numel() + self.Fh.numel() + self.sigh.numel()
+                          + self.Eh.numel()) * 8
+
+    def _compute(self, j):
+        H, rho, F, sig, vir, E = self.out[j]
+        self.use("vlocal")
+        self.g.vlocal(self.Vd[j], H, stream=self.stream)
+        self.use("rho")
+        self.g.rho(self.Dd[j], rho, stream=self.stream)
+        self.use("force")
+        self.g.force_stress(self.Vd[j], self.Dd[j], out=(F, sig, vir, E), stream=self.stream)
+
+    def _download(self, j):
+        H, rho, F, sig, _, E = self.out[j]
+        self.Hh.copy_(H, non_blocking=True)
+        self.rhoh.copy_(rho, non_blocking=True)
+        self.Fh.copy_(F, non_blocking=True)
+        self.sigh.copy_(sig, non_blocking=True)
+        self.Eh.copy_(E, non_blocking=True)
+
+    def step(self):
+        """One step with its copies on the compute stream."""
+        import torch
+        with torch.cuda.stream(self.stream):
+            self.Vd[0].copy_(self.Vh, non_blocking=True)
+            self.Dd[0].copy_(self.Dh, non_blocking=True)
+            self._compute(0)
+            self._download(0)
+
+    def inline(self, n):
+        """ms per step of n steps with the copies in line."""
+        import torch
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(self.stream)
+        for _ in range(n):
+            self.step()
+        b.record(self.stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    def overlapped(self, n):
+        """ms per step of n steps with overlapped copies, from the first upload to the last download."""
+        import torch
+        ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+        if self.Vd[1] is None:
+            self.Vd[1], self.Dd[1], self.out[1] = torch.empty_like(self.Vd[0]), torch.empty_like(self.Dd[0]), self._outs()
+        st = self.stream
+        cin, cout = torch.cuda.Stream(device=self.dev), torch.cuda.Stream(device=self.dev)
+        ev_in, ev_done, ev_out = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+        start, stop = ev(), ev()
+        start.record(st)
+        cin.wait_event(start)
+        with torch.cuda.stream(cin):
+            self.Vd[0].copy_(self.Vh, non_blocking=True)
+            self.Dd[0].copy_(self.Dh, non_blocking=True)
+        ev_in[0].record(cin)
+        for k in range(n):
+            j = k & 1
+            st.wait_event(ev_in[j])
+            if k >= 2:
+                st.wait_event(ev_out[j])  # the outputs of step k - 2 have been read back
+            self._compute(j)
+            ev_done[j].record(st)
+            if k + 1 < n:
+                if k >= 1:
+                    cin.wait_event(ev_done[1 - j])  # step k - 1 no longer reads inputs 1 - j
+                with torch.cuda.stream(cin):
+                    self.Vd[1 - j].copy_(self.Vh, non_blocking=True)
+                    self.Dd[1 - j].copy_(self.Dh, non_blocking=True)
+                ev_in[1 - j].record(cin)
+            cout.wait_event(ev_done[j])
+            with torch.cuda.stream(cout):  # one copy stream: downloads into the host buffers stay in order
+                self._download(j)
+            ev_out[j].record(cout)
+        st.wait_event(ev_out[(n - 1) & 1])
+        stop.record(st)
+        torch.cuda.synchronize()
+        return start.elapsed_time(stop) / n
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -369,103 +480,18 @@ def run_ours(args):
     # ---- end to end through the public API with host buffers
     e2e = None
     if args.e2e_steps > 0:
-        Vh = V.cpu().pin_memory()
-        Dh = D.cpu().pin_memory()
-        Hh = torch.empty(H.shape, dtype=H.dtype).pin_memory()
-        rhoh = torch.empty(rho.shape, dtype=rho.dtype).pin_memory()
-        Fh = torch.empty(F.shape, dtype=F.dtype).pin_memory()
-        sigh = torch.empty(sig.shape, dtype=sig.dtype).pin_memory()
-        Eh = torch.empty(E.shape, dtype=E.dtype).pin_memory()
-        Vd = torch.empty_like(V)
-        Dd = torch.empty_like(D)
-
-        def e2e_step():
-            Vd.copy_(Vh, non_blocking=True)
-            Dd.copy_(Dh, non_blocking=True)
-            use("vlocal")
-            g.vlocal(Vd, H, stream=stream)
-            use("rho")
-            g.rho(Dd, rho, stream=stream)
-            use("force")
-            g.force_stress(Vd, Dd, out=(F, sig, vir, E), stream=stream)
-            Hh.copy_(H, non_blocking=True)
-            rhoh.copy_(rho, non_blocking=True)
-            Fh.copy_(F, non_blocking=True)
-            sigh.copy_(sig, non_blocking=True)
-            Eh.copy_(E, non_blocking=True)
-
-        def e2e_overlapped(n):
-            """The same n steps with the copies of neighbouring steps overlapped: the upload of
-            step k + 1 and the download of step k run on two copy streams while step k + 1
-            computes, ordered by events; two sets of device inputs and outputs.  Returns ms per
-            step from the first upload to the last download."""
-            cin, cout = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-            Vb, Db = [Vd, torch.empty_like(V)], [Dd, torch.empty_like(D)]
-            Hb, rb = [H, torch.empty_like(H)], [rho, torch.empty_like(rho)]
-            Fb, sb = [F, torch.empty_like(F)], [sig, torch.empty_like(sig)]
-            vb, Eb = [vir, torch.empty_like(vir)], [E, torch.empty_like(E)]
-            ev_in, ev_done, ev_out = [ev(), ev()], [ev(), ev()], [ev(), ev()]
-            start, stop = ev(), ev()
-            start.record(stream)
-            cin.wait_event(start)
-            with torch.cuda.stream(cin):
-                Vb[0].copy_(Vh, non_blocking=True)
-                Db[0].copy_(Dh, non_blocking=True)
-            ev_in[0].record(cin)
-            for k in range(n):
-                j = k & 1
-                stream.wait_event(ev_in[j])
-                if k >= 2:
-                    stream.wait_event(ev_out[j])  # the outputs of step k - 2 have been read back
-                use("vlocal")
-                g.vlocal(Vb[j], Hb[j], stream=stream)
-                use("rho")
-                g.rho(Db[j], rb[j], stream=stream)
-                use("force")
-                g.force_stress(Vb[j], Db[j], out=(Fb[j], sb[j], vb[j], Eb[j]), stream=stream)
-                ev_done[j].record(stream)
-                if k + 1 < n:
-                    if k >= 1:
-                        cin.wait_event(ev_done[1 - j])  # step k - 1 no longer reads inputs 1 - j
-                    with torch.cuda.stream(cin):
-                        Vb[1 - j].copy_(Vh, non_blocking=True)
-                        Db[1 - j].copy_(Dh, non_blocking=True)
-                    ev_in[1 - j].record(cin)
-                cout.wait_event(ev_done[j])
-                with torch.cuda.stream(cout):
-                    Hh.copy_(Hb[j], non_blocking=True)
-                    rhoh.copy_(rb[j], non_blocking=True)
-                    Fh.copy_(Fb[j], non_blocking=True)
-                    sigh.copy_(sb[j], non_blocking=True)
-                    Eh.copy_(Eb[j], non_blocking=True)
-                ev_out[j].record(cout)
-            stream.wait_event(ev_out[(n - 1) & 1])
-            stop.record(stream)
-            torch.cuda.synchronize()
-            return start.elapsed_time(stop) / n
-
-        e2e_step()
+        runner = EndToEnd(g, V, D, use, stream, dev)
+        runner.step()
         torch.cuda.synchronize()
         barrier()
-        if args.e2e_overlap:
-            ms_one = e2e_overlapped(args.e2e_steps)
-        else:
-            a, b = ev(), ev()
-            a.record(stream)
-            for _ in range(args.e2e_steps):
-                e2e_step()
-            b.record(stream)
-            torch.cuda.synchronize()
-            ms_one = a.elapsed_time(b) / args.e2e_steps
+        ms_one = runner.overlapped(args.e2e_steps) if args.e2e_overlap else runner.inline(args.e2e_steps)
         barrier()
         g.sync()
         ms_e2e = max_over_ranks(ms_one, ws, dev)
-        h2d = (Vh.numel() + Dh.numel()) * 8
-        d2h = (Hh.numel() + rhoh.numel() + Fh.numel() + sigh.numel() + Eh.numel()) * 8
-        e2e = {"value": whole_job_rate(ng, 1, ws, ms_e2e), "unit": "grid_points/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
+        e2e = {"value": whole_job_rate(ng, 1, ws, ms_e2e), "unit": "grid_points/s",
+               "h2d_bytes_per_step": runner.h2d_bytes, "d2h_bytes_per_step": runner.d2h_bytes, "ms_per_step": ms_e2e,
                "copies": "overlapped with the neighbouring steps" if args.e2e_overlap else "in line with the step"}
-        del Vh, Dh, Hh, rhoh, Vd, Dd
+        del runner
 
     # ---- roofline of the dominant call
     peaks, peak_src = load_peaks()

@@ -68,11 +68,16 @@ typedef enum {
 typedef enum {
     GINT_FP64 = 0,
     GINT_FP32 = 1,     /* FP32 orbital values and FP32 SIMT contractions */
-    GINT_TF32 = 2,     /* reserved */
+    GINT_TF32 = 2,     /* not implemented (GINT_ERR_UNSUPPORTED): TF32 keeps 10 mantissa bits per
+                          operand and accumulates in FP32 like the 16-bit splits, so it has their
+                          accumulation bias without their 22-bit operands */
     GINT_BF16X3 = 3,   /* H^V, rho and force on the tensor cores: operands split
                           x = hi + lo in bf16, products hi*hi + hi*lo + lo*hi, FP32
                           accumulation per brick (H^V) or per 128-point tile (rho, force) */
-    GINT_BF16X6 = 4,   /* reserved */
+    GINT_BF16X6 = 4,   /* not implemented (GINT_ERR_UNSUPPORTED): a three-piece split with six
+                          products; GINT_FP16X4 below is the ~FP32-accurate split this library
+                          provides (its leading term accumulates exactly, which a six-product
+                          bf16 split would not) */
     GINT_FP16X3 = 5,   /* as GINT_BF16X3 with fp16 pieces (22-bit products) */
     GINT_FP16X4 = 6    /* tensor cores, exact leading term: each operand value x is written
                           x / q = n + l1 + l2 with q a power of two (per orbital for the
@@ -123,7 +128,8 @@ void gint_destroy(gint_handle* h);
 /* The pair pattern.  *blocks points to device memory holding n_blocks rows of
  * (I, J, t1, t2, t3) int32; *offsets to device memory holding n_blocks+1 int64
  * element offsets (offsets[n_blocks] = n_values).  Both stay owned by the
- * handle and valid until gint_destroy.  Any output pointer may be NULL. */
+ * handle and valid until gint_destroy or gint_update_positions.  Any output
+ * pointer may be NULL. */
 gint_status gint_pattern(const gint_handle* h, int64_t* n_blocks, int64_t* n_values,
                          const int32_t** blocks, const int64_t** offsets);
 
@@ -160,16 +166,77 @@ gint_status gint_rho(gint_handle* h, const double* D, double* rho, gint_stream s
 gint_status gint_force_stress(gint_handle* h, const double* V, const double* D, double* F,
                               double* sigma, double* virial_atom, double* E, gint_stream stream);
 
+/* Gradients of the grid energy E = sum_g V_g rho_g[D] dV = sum_blocks D . H^V (Eq. 2-5), the
+ * adjoint of the three calls above, each output re-evaluating the orbital values (nothing is
+ * kept from an earlier call):
+ *   dE_dR[n_atoms][3]   dE/dR_I = -F_I                        (Eq. 4, at fixed V and D)
+ *   dE_deps[3][3]       dE/d(eps_ab) = sum_I Pi_I = -Omega sigma  (Eq. 5, homogeneous strain of
+ *                       atoms, images and grid points at fixed V_g and dV)
+ *   dE_dV[n1][n2][n3]   dE/dV_g = rho_g dV                    (Eq. 3)
+ *   dE_dD (n_values)    dE/dD = H^V on every block of the pattern (Eq. 2)
+ *   E[1]                E itself (not scaled)
+ * Every gradient is multiplied by *grad_E (a device scalar, the upstream gradient of a
+ * reverse-mode chain; NULL means 1).  All pointers are device memory of the handle's device;
+ * NULL outputs are skipped, at least one must be non-NULL.  V and D as for gint_force_stress
+ * (D symmetric, canonical blocks read).  Errors as for gint_force_stress. */
+gint_status gint_energy_grads(gint_handle* h, const double* V, const double* D, const double* grad_E, double* dE_dR,
+                              double* dE_deps, double* dE_dV, double* dE_dD, double* E, gint_stream stream);
+
+/* New atom positions (and optionally a new cell) for an existing handle: the pair pattern,
+ * the atom images, the brick lists, pair tables and tile masks are rebuilt for the new
+ * geometry in place (the handle pointer stays valid); the grid dimensions, species tables,
+ * precision, brick shape, brick selection and wait limit are kept.  This is the step of the
+ * ionic loop of the paper's Fig. 1 between two force evaluations.
+ *   pos[n_atoms][3] (host, bohr); cell[9] (host) or NULL to keep the cell.
+ *   keep_pattern = 1: the new geometry must have exactly the same pattern (so D and H laid
+ *     out on it stay valid, e.g. for small displacements); if it does not, nothing changes and
+ *     GINT_ERR_PATTERN_MISMATCH is returned.
+ *   keep_pattern = 0: the pattern may change; *pattern_changed (may be NULL) is set to 1 if it
+ *     did (then gint_pattern gives the new block list and offsets).
+ * Synchronous (waits for the device).  On any error the handle is unchanged.  Batches made
+ * from the handle before the call are stale: gint_batch_run rejects them. */
+gint_status gint_update_positions(gint_handle* h, const double* pos, const double* cell, int keep_pattern,
+                                  int* pattern_changed);
+
+/* Restrict later calls to a subset of the bricks (the batches of grid points of Section 2.3.2),
+ * the unit of work that the paper's task decomposition deals to processes (Section 2.3.1,
+ * Fig. 5).  Brick b covers grid points [b0 B0, (b0+1) B0) x [b1 B1, ...) x [b2 B2, ...) with
+ * b = (b0 nb1 + b1) nb2 + b2, nb_i = ceil(n_i / B_i), B the brick shape (gint_get_info).
+ *   bricks: host array of n brick ids in [0, nb0 nb1 nb2) (duplicates allowed), or NULL for every
+ *   brick (the default).
+ * With a selection, gint_vlocal and gint_force_stress return the contributions of the selected
+ * bricks' grid points only (the results of disjoint selections covering the grid add up to the
+ * full results), and gint_rho writes rho on the selected bricks' points only (other elements are
+ * left untouched).  Synchronous; GINT_ERR_INVALID_ARG for an id out of range. */
+gint_status gint_select_bricks(gint_handle* h, int64_t n, const int64_t* bricks);
+
+/* Work of every brick, for partitioning the bricks by cost: n_images[b] (host, one entry per
+ * brick, n_bricks of gint_get_info) = number of atom images whose cutoff sphere meets brick b. */
+gint_status gint_brick_loads(const gint_handle* h, int64_t* n_images);
+
+/* Number of polls after which a wait of the tensor-core pipelines (producers, copies and MMA
+ * issue handing buffers to one another) gives up: the kernel then stops its work, raises a
+ * flag that gint_sync reports as GINT_ERR_TIMEOUT, and returns.  0 = the default (2^26 polls,
+ * far above any normal wait).  The waits that drain the tensor pipe before tensor memory is
+ * released always use the default.  Host only. */
+gint_status gint_set_wait_limit(gint_handle* h, int64_t polls);
+
+/* Test hook: the n-th device allocation the library makes from now on (n >= 1) fails the way
+ * cudaMalloc fails on a full device, so that out-of-memory paths can be exercised without
+ * filling a GPU; 0 disables.  Process-wide.  gint_setup then returns GINT_ERR_OOM having
+ * released everything it allocated. */
+gint_status gint_debug_fail_alloc(int n);
+
 /* H^V in the FP64 form, like gint_vlocal(h, V, H, 0, stream), without any
  * device allocation.  For callers that cannot let a library call cudaMalloc
  * (it synchronises the device and fails once a framework's caching allocator
  * has reserved the free memory): the kernel's orbital-value scratch is a fixed
- * 64 MiB array inside libgint, present on every GPU that loads the library
- * until the process exits.  The paper has no counterpart of this call.
+ * 64 MiB array inside libgint.  The paper has no counterpart of this call.
  *   - Always FP64, whatever gint_set_precision selected; H is overwritten.
- *   - The first call on a device resolves the array's device address
- *     (cudaGetSymbolAddress, with the handle's device current); make that first
- *     call before any stream capture.
+ *   - gint_setup maps the array on the handle's device (cudaGetSymbolAddress,
+ *     with that device current), which reserves its 64 MiB there until the
+ *     process exits; the call itself only reads the address kept in the handle.
+ *     If the mapping failed at set-up, the call returns GINT_ERR_CUDA.
  *   - A brick whose scratch slice exceeds 64 MiB is rejected with
  *     GINT_ERR_UNSUPPORTED (use smaller bricks); with fewer slices than the
  *     handle's CTA count the kernel runs on fewer CTAs.

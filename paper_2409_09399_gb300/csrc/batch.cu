@@ -22,6 +22,7 @@ struct gint_batch {
     int device = 0;
     int form = -1;  // tensor-core form shared by every cell (queue path), -1: per-cell calls
     std::vector<gint_handle*> h;
+    std::vector<int> gen;            // each handle's generation when the batch was made
     std::vector<int> item0;          // first queue item of each cell
     int n_items = 0;
     gint::CellJob* d_jobs = nullptr;  // device table of the cells' jobs
@@ -99,6 +100,7 @@ gint_status gint_batch_create(int n, gint_handle* const* handles, gint_batch** o
     b->n = n;
     b->device = dev;
     b->h.assign(handles, handles + n);
+    for (int i = 0; i < n; ++i) b->gen.push_back(handles[i]->generation);
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
@@ -128,11 +130,11 @@ gint_status gint_batch_create(int n, gint_handle* const* handles, gint_batch** o
                 item_cell.insert(item_cell.end(), (size_t)b->h[i]->n_work, i);
             }
             b->n_items = (int)item_cell.size();
-            e = cudaMalloc(&b->d_item_cell, sizeof(int) * std::max<size_t>(1, item_cell.size()));
+            e = dev_malloc(&b->d_item_cell, sizeof(int) * std::max<size_t>(1, item_cell.size()));
             if (e == cudaSuccess && !item_cell.empty())
                 e = cudaMemcpy(b->d_item_cell, item_cell.data(), sizeof(int) * item_cell.size(), cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = cudaMalloc(&b->d_jobs, sizeof(CellJob) * n);
-            if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
+            if (e == cudaSuccess) e = dev_malloc(&b->d_jobs, sizeof(CellJob) * n);
+            if (e == cudaSuccess) e = dev_malloc(&b->d_counter, sizeof(int));
             if (e != cudaSuccess) { set_error("gint_batch_create: %s", cudaGetErrorString(e)); s = GINT_ERR_CUDA; }
         }
     }
@@ -174,6 +176,12 @@ gint_status gint_batch_run(gint_batch* b, const double* const* V, const double* 
     set_error("");
     if (!b || !V || !D) { set_error("gint_batch_run: NULL argument"); return GINT_ERR_INVALID_ARG; }
     const int n = b->n;
+    for (int i = 0; i < n; ++i)
+        if (b->h[i]->generation != b->gen[i]) {
+            set_error("gint_batch_run: cell %d's handle changed (gint_update_positions or gint_select_bricks) after "
+                      "gint_batch_create; create the batch again", i);
+            return GINT_ERR_INVALID_ARG;
+        }
     std::vector<const void*> key;
     key.reserve((size_t)7 * n);
     for (int i = 0; i < n; ++i) {

@@ -9,6 +9,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/gint.h"
@@ -191,6 +192,17 @@ struct gint_handle {
     size_t scratch_bytes = 0;
     int n_ctas = 0;                   // persistent CTAs of the SIMT kernels
     int sm_count = 0;
+    void* d_static = nullptr;         // device address of the library's static scratch array (not owned)
+    long long wait_limit = 0;         // polls of a bounded tensor-core pipeline wait (0: the default)
+    int generation = 0;               // bumped by gint_update_positions (batches built earlier are stale)
+    int brick_opt[3] = {0, 0, 0};     // brick shape asked for at set-up (0: default)
+    // host copy of the species tables and the atoms' species, for gint_update_positions
+    std::vector<double> sp_rc;
+    std::vector<int> sp_nrad, rad_l, rad_nk, atom_species;
+    std::vector<double> rad_dr, rad_y, rad_dy;
+    // bricks selected by gint_select_bricks (selecting == false: every brick)
+    bool selecting = false;
+    std::vector<int64_t> selection;
 
     gint::Problem problem() const {
         gint::Problem p;
@@ -221,6 +233,18 @@ namespace gint {
 
 // last-error message (thread local), set by the ABI layer
 void set_error(const char* fmt, ...);
+
+// Every device allocation of the library goes through dev_malloc, which a test hook
+// (gint_debug_fail_alloc) can make fail as cudaMalloc does when the device is full.
+cudaError_t dev_malloc_raw(void** p, size_t bytes);
+template <typename T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) { return dev_malloc_raw(reinterpret_cast<void**>(p), bytes); }
+
+// Polls of a bounded wait on the tensor-core pipelines (gint_set_wait_limit); the drains before
+// tensor memory is released always use kDrainPolls.
+constexpr long kDefaultWaitPolls = 1L << 26;
+constexpr long kDrainPolls = 1L << 26;
+inline long wait_polls(const gint_handle* h) { return h->wait_limit > 0 ? (long)h->wait_limit : kDefaultWaitPolls; }
 
 #define GINT_CUDA_TRY(expr)                                                                     \
     do {                                                                                        \

@@ -8,10 +8,9 @@
 // and some host code (schedulers with a fixed memory plan, allocator hooks)
 // must not enter the CUDA allocator at all.  gint_vlocal_static runs the same
 // FP64 kernel with its scratch in a fixed-size array that is part of the
-// library image (kStaticScratchBytes per GPU, held from library load to
-// process exit) and calls no allocating routine.
-#include <mutex>
-
+// library image (kStaticScratchBytes per GPU, reserved when gint_setup first
+// runs on that GPU and held until the process exits) and calls no allocating
+// routine.
 #include "gint_impl.cuh"
 
 namespace gint {
@@ -20,32 +19,23 @@ gint_status simt_vlocal_on_scratch(gint_handle* h, const double* V, double* H, c
                                    int n_ctas, cudaStream_t st);
 gint_status launch_mirror(gint_handle* h, double* H, cudaStream_t st);
 
-constexpr size_t kStaticScratchBytes = size_t(64) << 20;  // 64 MiB on every GPU that loads the library
-constexpr int kMaxDevices = 64;
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;  // 64 MiB on every GPU that maps the array
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-static std::mutex g_static_mu;
-static void* g_static_addr[kMaxDevices];
-
-// Device address of g_static_scratch on `dev` (which must be current), resolved
-// once per device.  In host code the symbol is only a stand-in.
-static gint_status static_scratch_address(int dev, void** out) {
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("device ordinal %d out of range", dev);
-        return GINT_ERR_INVALID_ARG;
+// Device address of g_static_scratch on the current device.  Called by gint_setup, with the
+// handle's device current, so that the module holding the array is loaded (and its 64 MiB
+// reserved) at set-up, where allocating is allowed, rather than by the first
+// gint_vlocal_static.  In host code the symbol itself is only a stand-in for that address.
+gint_status static_scratch_resolve(void** out) {
+    *out = nullptr;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error("cudaGetSymbolAddress of the static scratch array failed: %s", cudaGetErrorString(e));
+        return GINT_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error("cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
-            return GINT_ERR_CUDA;
-        }
-        g_static_addr[dev] = p;
-    }
-    *out = g_static_addr[dev];
+    *out = p;
     return GINT_OK;
 }
 
@@ -72,8 +62,11 @@ extern "C" gint_status gint_vlocal_static(gint_handle* h, const double* V, doubl
         return GINT_ERR_CUDA;
     }
     gint_status s = GINT_OK;
-    void* scratch = nullptr;
-    s = static_scratch_address(h->device, &scratch);
+    void* scratch = h->d_static;  // resolved by gint_setup on this device
+    if (!scratch) {
+        set_error("gint_vlocal_static: the static scratch array was not mapped when the handle was set up");
+        s = GINT_ERR_CUDA;
+    }
     if (s == GINT_OK) {
         cudaStream_t st = (cudaStream_t)stream;
         const int by_size = (int)(kStaticScratchBytes / per_cta);

@@ -6,6 +6,7 @@
 // points it lists, on the device, the atom images whose cutoff sphere meets
 // the brick (the "neighbouring atoms" of that batch).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -84,7 +85,7 @@ static gint_status scan_exclusive(const int64_t* in, int64_t n, int64_t* out, cu
         return GINT_OK;
     }
     int64_t* sums = nullptr;
-    GINT_CUDA_TRY(cudaMalloc(&sums, sizeof(int64_t) * (tiles + 1)));
+    GINT_CUDA_TRY(dev_malloc(&sums, sizeof(int64_t) * (tiles + 1)));
     k_scan_tile_sums<<<(unsigned)tiles, kScanTile, 0, st>>>(in, n, sums);
     k_scan_serial<<<1, 32, 0, st>>>(sums, tiles, sums + tiles);
     k_scan_apply<<<(unsigned)tiles, kScanTile, 0, st>>>(in, n, sums, out);
@@ -546,6 +547,20 @@ __global__ void k_work_stats(Problem P, unsigned long long* out) {
     }
 }
 
+// ----------------------------------------------------- allocation hook
+// gint_debug_fail_alloc(n): the n-th device allocation from then on fails the way cudaMalloc
+// fails on a full device (cudaErrorMemoryAllocation), without touching the device.
+static std::atomic<int> g_fail_alloc{0};
+
+cudaError_t dev_malloc_raw(void** p, size_t bytes) {
+    *p = nullptr;
+    int n = g_fail_alloc.load();
+    while (n > 0 && !g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 1) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
 // ----------------------------------------------------------- host helpers
 static void inv3(const double a[9], double out[9]) {
     double d = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) + a[2] * (a[3] * a[7] - a[4] * a[6]);
@@ -564,7 +579,7 @@ template <typename T>
 static gint_status dev_upload(T** dst, const T* src, size_t n) {
     *dst = nullptr;
     if (n == 0) n = 1;
-    GINT_CUDA_TRY(cudaMalloc((void**)dst, sizeof(T) * n));
+    GINT_CUDA_TRY(dev_malloc((void**)dst, sizeof(T) * n));
     if (src) GINT_CUDA_TRY(cudaMemcpy(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice));
     return GINT_OK;
 }
@@ -576,6 +591,7 @@ static gint_status dev_upload(T** dst, const T* src, size_t n) {
     } while (0)
 
 gint_status allocate_scratch(gint_handle* h);  // simt.cu
+gint_status static_scratch_resolve(void** out);  // noalloc.cu
 
 static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, const int* species, const double* cell,
                                 int n_species, const gint_species* sp, const int* grid, const gint_options* opt) {
@@ -724,13 +740,13 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
 
     // ---- pattern (Section 2.2 sparsity): rows I, sorted (J, t)
     int64_t *d_rc_cnt = nullptr, *d_rv = nullptr;
-    GINT_CUDA_TRY(cudaMalloc(&d_rc_cnt, sizeof(int64_t) * (n_atoms + 1)));
-    GINT_CUDA_TRY(cudaMalloc(&d_rv, sizeof(int64_t) * (n_atoms + 1)));
+    GINT_CUDA_TRY(dev_malloc(&d_rc_cnt, sizeof(int64_t) * (n_atoms + 1)));
+    GINT_CUDA_TRY(dev_malloc(&d_rv, sizeof(int64_t) * (n_atoms + 1)));
     tmp.p.push_back(d_rc_cnt);
     tmp.p.push_back(d_rv);
     k_pattern_count<<<n_atoms, 256, 0, st>>>(c, n_atoms, d_pos, d_spc, d_rc, d_nw, d_rc_cnt, d_rv);
     GINT_CUDA_TRY(cudaGetLastError());
-    GINT_CUDA_TRY(cudaMalloc(&h->d_row_start, sizeof(int64_t) * (n_atoms + 1)));
+    GINT_CUDA_TRY(dev_malloc(&h->d_row_start, sizeof(int64_t) * (n_atoms + 1)));
     GINT_TRY(scan_exclusive(d_rc_cnt, n_atoms, h->d_row_start, st));
     GINT_TRY(scan_exclusive(d_rv, n_atoms, d_rv, st));
     GINT_CUDA_TRY(cudaMemcpy(&h->n_blocks, h->d_row_start + n_atoms, sizeof(int64_t), cudaMemcpyDeviceToHost));
@@ -739,16 +755,16 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
         set_error("pattern has too many blocks (%lld)", (long long)h->n_blocks);
         return GINT_ERR_UNSUPPORTED;
     }
-    GINT_CUDA_TRY(cudaMalloc(&h->d_blocks, sizeof(int32_t) * 5 * std::max<int64_t>(1, h->n_blocks)));
-    GINT_CUDA_TRY(cudaMalloc(&h->d_offsets, sizeof(int64_t) * (h->n_blocks + 1)));
+    GINT_CUDA_TRY(dev_malloc(&h->d_blocks, sizeof(int32_t) * 5 * std::max<int64_t>(1, h->n_blocks)));
+    GINT_CUDA_TRY(dev_malloc(&h->d_offsets, sizeof(int64_t) * (h->n_blocks + 1)));
     k_pattern_fill<<<n_atoms, 256, 0, st>>>(c, n_atoms, d_pos, d_spc, d_rc, d_nw, h->d_row_start, d_rv, h->d_blocks,
                                             h->d_offsets);
     GINT_CUDA_TRY(cudaGetLastError());
     GINT_CUDA_TRY(cudaMemcpy(h->d_offsets + h->n_blocks, &h->n_values, sizeof(int64_t), cudaMemcpyHostToDevice));
-    GINT_CUDA_TRY(cudaMalloc(&h->d_err, sizeof(int) * 4));
+    GINT_CUDA_TRY(dev_malloc(&h->d_err, sizeof(int) * 4));
     GINT_CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(int) * 4));
-    GINT_CUDA_TRY(cudaMalloc(&h->d_red, sizeof(double) * 64));
-    GINT_CUDA_TRY(cudaMalloc(&h->d_facc, sizeof(double) * 12 * n_atoms));
+    GINT_CUDA_TRY(dev_malloc(&h->d_red, sizeof(double) * 64));
+    GINT_CUDA_TRY(dev_malloc(&h->d_facc, sizeof(double) * 12 * n_atoms));
     {
         std::vector<int> nwa(n_atoms);
         for (int i = 0; i < n_atoms; ++i) nwa[i] = nw_sp[spc[i]];
@@ -759,7 +775,7 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
         h->n_orbitals = oo[n_atoms];
         GINT_TRY(dev_upload(&h->d_orb_off, oo.data(), oo.size()));
     }
-    GINT_CUDA_TRY(cudaMalloc(&h->d_mirror, sizeof(int32_t) * std::max<int64_t>(1, h->n_blocks)));
+    GINT_CUDA_TRY(dev_malloc(&h->d_mirror, sizeof(int32_t) * std::max<int64_t>(1, h->n_blocks)));
     {
         Problem P = h->problem();
         int64_t nb = h->n_blocks;
@@ -803,8 +819,8 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
     // ---- binner
     int64_t nbk = h->n_bricks;
     int64_t *d_count = nullptr, *d_fill = nullptr;
-    GINT_CUDA_TRY(cudaMalloc(&d_count, sizeof(int64_t) * (nbk + 1)));
-    GINT_CUDA_TRY(cudaMalloc(&d_fill, sizeof(int64_t) * (nbk + 1)));
+    GINT_CUDA_TRY(dev_malloc(&d_count, sizeof(int64_t) * (nbk + 1)));
+    GINT_CUDA_TRY(dev_malloc(&d_fill, sizeof(int64_t) * (nbk + 1)));
     tmp.p.push_back(d_count);
     tmp.p.push_back(d_fill);
     GINT_CUDA_TRY(cudaMemset(d_count, 0, sizeof(int64_t) * (nbk + 1)));
@@ -818,10 +834,10 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
     unsigned nblk = (unsigned)((h->n_ext * 32 + 255) / 256);
     if (h->n_ext > 0) k_bin<<<nblk, 256, 0, st>>>(ba, 0, d_count, nullptr, nullptr, nullptr);
     GINT_CUDA_TRY(cudaGetLastError());
-    GINT_CUDA_TRY(cudaMalloc(&h->d_brick_start, sizeof(int64_t) * (nbk + 1)));
+    GINT_CUDA_TRY(dev_malloc(&h->d_brick_start, sizeof(int64_t) * (nbk + 1)));
     GINT_TRY(scan_exclusive(d_count, nbk, h->d_brick_start, st));
     GINT_CUDA_TRY(cudaMemcpy(&h->n_brick_atoms, h->d_brick_start + nbk, sizeof(int64_t), cudaMemcpyDeviceToHost));
-    GINT_CUDA_TRY(cudaMalloc(&h->d_brick_atoms, sizeof(int32_t) * std::max<int64_t>(1, h->n_brick_atoms)));
+    GINT_CUDA_TRY(dev_malloc(&h->d_brick_atoms, sizeof(int32_t) * std::max<int64_t>(1, h->n_brick_atoms)));
     if (h->n_ext > 0) k_bin<<<nblk, 256, 0, st>>>(ba, 1, nullptr, h->d_brick_start, d_fill, h->d_brick_atoms);
     GINT_CUDA_TRY(cudaGetLastError());
     k_sort_bricks<<<(unsigned)((nbk * 32 + 255) / 256), 256, 0, st>>>(nbk, h->d_brick_start, h->d_brick_atoms, h->d_err);
@@ -831,11 +847,11 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
     int64_t *d_flag = nullptr, *d_pairs = nullptr, *d_pos_ne = nullptr;
     int* d_max = nullptr;
     unsigned long long* d_sum = nullptr;
-    GINT_CUDA_TRY(cudaMalloc(&d_flag, sizeof(int64_t) * (nbk + 1)));
-    GINT_CUDA_TRY(cudaMalloc(&d_pairs, sizeof(int64_t) * (nbk + 1)));
-    GINT_CUDA_TRY(cudaMalloc(&d_pos_ne, sizeof(int64_t) * (nbk + 1)));
-    GINT_CUDA_TRY(cudaMalloc(&d_max, sizeof(int) * 2));
-    GINT_CUDA_TRY(cudaMalloc(&d_sum, sizeof(unsigned long long)));
+    GINT_CUDA_TRY(dev_malloc(&d_flag, sizeof(int64_t) * (nbk + 1)));
+    GINT_CUDA_TRY(dev_malloc(&d_pairs, sizeof(int64_t) * (nbk + 1)));
+    GINT_CUDA_TRY(dev_malloc(&d_pos_ne, sizeof(int64_t) * (nbk + 1)));
+    GINT_CUDA_TRY(dev_malloc(&d_max, sizeof(int) * 2));
+    GINT_CUDA_TRY(dev_malloc(&d_sum, sizeof(unsigned long long)));
     tmp.p.push_back(d_flag);
     tmp.p.push_back(d_pairs);
     tmp.p.push_back(d_pos_ne);
@@ -853,15 +869,15 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
     // ---- per-brick pair tables
     {
         int64_t* d_pcnt = nullptr;
-        GINT_CUDA_TRY(cudaMalloc(&d_pcnt, sizeof(int64_t) * (nbk + 1)));
+        GINT_CUDA_TRY(dev_malloc(&d_pcnt, sizeof(int64_t) * (nbk + 1)));
         tmp.p.push_back(d_pcnt);
         k_pair_count<<<(unsigned)((nbk + 255) / 256), 256, 0, st>>>(nbk, h->d_brick_start, d_pcnt);
         GINT_CUDA_TRY(cudaGetLastError());
-        GINT_CUDA_TRY(cudaMalloc(&h->d_pair_start, sizeof(int64_t) * (nbk + 1)));
+        GINT_CUDA_TRY(dev_malloc(&h->d_pair_start, sizeof(int64_t) * (nbk + 1)));
         GINT_TRY(scan_exclusive(d_pcnt, nbk, h->d_pair_start, st));
         int64_t n_pair_entries = 0;
         GINT_CUDA_TRY(cudaMemcpy(&n_pair_entries, h->d_pair_start + nbk, sizeof(int64_t), cudaMemcpyDeviceToHost));
-        GINT_CUDA_TRY(cudaMalloc(&h->d_pairs, sizeof(int32_t) * std::max<int64_t>(1, n_pair_entries)));
+        GINT_CUDA_TRY(dev_malloc(&h->d_pairs, sizeof(int32_t) * std::max<int64_t>(1, n_pair_entries)));
         Problem P = h->problem();
         k_brick_pairs<<<(unsigned)((nbk * 32 + 255) / 256), 256, 0, st>>>(P, nbk, d_rc, h->d_pairs);
         GINT_CUDA_TRY(cudaGetLastError());
@@ -869,14 +885,14 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
     GINT_TRY(scan_exclusive(d_flag, nbk, d_pos_ne, st));
     GINT_CUDA_TRY(cudaMemcpy(&h->n_work, d_pos_ne + nbk, sizeof(int64_t), cudaMemcpyDeviceToHost));
     h->n_empty = nbk - h->n_work;
-    GINT_CUDA_TRY(cudaMalloc(&h->d_work, sizeof(int32_t) * std::max<int64_t>(1, h->n_work)));
-    GINT_CUDA_TRY(cudaMalloc(&h->d_empty, sizeof(int32_t) * std::max<int64_t>(1, h->n_empty)));
+    GINT_CUDA_TRY(dev_malloc(&h->d_work, sizeof(int32_t) * std::max<int64_t>(1, h->n_work)));
+    GINT_CUDA_TRY(dev_malloc(&h->d_empty, sizeof(int32_t) * std::max<int64_t>(1, h->n_empty)));
     k_compact<<<(unsigned)((nbk + 255) / 256), 256, 0, st>>>(nbk, d_flag, d_pos_ne, h->d_work, h->d_empty, nullptr);
     GINT_CUDA_TRY(cudaGetLastError());
     {
         const int n_mt = (h->grid.bpad + 127) / 128;
         const int64_t n_masks = h->n_work * n_mt;
-        GINT_CUDA_TRY(cudaMalloc(&h->d_tile_mask, sizeof(unsigned long long) * std::max<int64_t>(1, n_masks)));
+        GINT_CUDA_TRY(dev_malloc(&h->d_tile_mask, sizeof(unsigned long long) * std::max<int64_t>(1, n_masks)));
         if (n_masks > 0) {
             Problem P = h->problem();
             k_tile_mask<<<(unsigned)((n_masks * 32 + 255) / 256), 256, 0, st>>>(P, n_mt, h->d_tile_mask);
@@ -902,6 +918,12 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
         return GINT_ERR_UNSUPPORTED;
     }
     GINT_TRY(allocate_scratch(h));
+    // the static scratch of gint_vlocal_static: map it now, while allocating is allowed (a failure
+    // here only disables that call, which then reports it)
+    if (static_scratch_resolve(&h->d_static) != GINT_OK) {
+        (void)cudaGetLastError();
+        set_error("");
+    }
     return GINT_OK;
 }
 
@@ -917,6 +939,89 @@ static void free_handle(gint_handle* h) {
         if (p) cudaFree(p);
     if (prev >= 0) cudaSetDevice(prev);
     delete h;
+}
+
+// Host copy of the species tables and the atoms' species (for gint_update_positions).
+static void store_species(gint_handle* h, int n_atoms, const int* species, int n_species, const gint_species* sp,
+                          const gint_options* opt) {
+    h->atom_species.assign(species, species + n_atoms);
+    h->sp_rc.clear(); h->sp_nrad.clear(); h->rad_l.clear(); h->rad_nk.clear();
+    h->rad_dr.clear(); h->rad_y.clear(); h->rad_dy.clear();
+    for (int s = 0; s < n_species; ++s) {
+        h->sp_rc.push_back(sp[s].rc);
+        h->sp_nrad.push_back(sp[s].n_radial);
+        for (int j = 0; j < sp[s].n_radial; ++j) {
+            const gint_radial& R = sp[s].radial[j];
+            h->rad_l.push_back(R.l);
+            h->rad_nk.push_back(R.n_knots);
+            h->rad_dr.push_back(R.dr);
+            h->rad_y.insert(h->rad_y.end(), R.y, R.y + R.n_knots);
+            h->rad_dy.insert(h->rad_dy.end(), R.dy, R.dy + R.n_knots);
+        }
+    }
+    for (int i = 0; i < 3; ++i) h->brick_opt[i] = opt ? opt->brick[i] : 0;
+}
+
+// gint_species views of the stored tables (pointers into h's vectors).
+static void species_views(const gint_handle* h, std::vector<gint_species>& S, std::vector<gint_radial>& R) {
+    R.resize(h->rad_l.size());
+    S.resize(h->sp_rc.size());
+    size_t j = 0, off = 0;
+    for (size_t s = 0; s < S.size(); ++s) {
+        S[s].rc = h->sp_rc[s];
+        S[s].n_radial = h->sp_nrad[s];
+        S[s].radial = R.data() + j;
+        for (int k = 0; k < h->sp_nrad[s]; ++k, ++j) {
+            R[j].l = h->rad_l[j];
+            R[j].n_knots = h->rad_nk[j];
+            R[j].dr = h->rad_dr[j];
+            R[j].y = h->rad_y.data() + off;
+            R[j].dy = h->rad_dy.data() + off;
+            off += (size_t)h->rad_nk[j];
+        }
+    }
+}
+
+// Work lists (non-empty and empty bricks, natural order) of the selected bricks, and the
+// tile masks of the new work list.  Synchronous.
+static gint_status rebuild_work_lists(gint_handle* h) {
+    const int64_t nbk = h->n_bricks;
+    std::vector<int64_t> bs(nbk + 1);
+    GINT_CUDA_TRY(cudaMemcpy(bs.data(), h->d_brick_start, sizeof(int64_t) * (nbk + 1), cudaMemcpyDeviceToHost));
+    std::vector<char> sel(nbk, h->selecting ? 0 : 1);
+    for (int64_t b : h->selection) sel[b] = 1;
+    std::vector<int32_t> work, empty;
+    for (int64_t b = 0; b < nbk; ++b)
+        if (sel[b]) (bs[b + 1] > bs[b] ? work : empty).push_back((int32_t)b);
+    int32_t *d_work = nullptr, *d_empty = nullptr;
+    unsigned long long* d_mask = nullptr;
+    const int n_mt = (h->grid.bpad + 127) / 128;
+    const int64_t n_masks = (int64_t)work.size() * n_mt;
+    cudaError_t e = dev_malloc(&d_work, sizeof(int32_t) * std::max<size_t>(1, work.size()));
+    if (e == cudaSuccess) e = dev_malloc(&d_empty, sizeof(int32_t) * std::max<size_t>(1, empty.size()));
+    if (e == cudaSuccess) e = dev_malloc(&d_mask, sizeof(unsigned long long) * std::max<int64_t>(1, n_masks));
+    if (e == cudaSuccess && !work.empty())
+        e = cudaMemcpy(d_work, work.data(), sizeof(int32_t) * work.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !empty.empty())
+        e = cudaMemcpy(d_empty, empty.data(), sizeof(int32_t) * empty.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d_work); cudaFree(d_empty); cudaFree(d_mask);
+        set_error("selecting bricks: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? GINT_ERR_OOM : GINT_ERR_CUDA;
+    }
+    cudaFree(h->d_work); cudaFree(h->d_empty); cudaFree(h->d_tile_mask);
+    h->d_work = d_work;
+    h->d_empty = d_empty;
+    h->d_tile_mask = d_mask;
+    h->n_work = (int64_t)work.size();
+    h->n_empty = (int64_t)empty.size();
+    if (n_masks > 0) {
+        Problem P = h->problem();
+        k_tile_mask<<<(unsigned)((n_masks * 32 + 255) / 256), 256>>>(P, n_mt, h->d_tile_mask);
+        GINT_CUDA_TRY(cudaGetLastError());
+    }
+    GINT_CUDA_TRY(cudaDeviceSynchronize());
+    return GINT_OK;
 }
 
 }  // namespace gint
@@ -995,6 +1100,7 @@ gint_status gint_setup(int n_atoms, const double* pos, const int* species, const
     h->n_species = n_species;
     h->precision = opt ? opt->precision : GINT_FP64;
     cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    store_species(h, n_atoms, species, n_species, sp, opt);
     gint_status st = build_handle(h, n_atoms, pos, species, cell, n_species, sp, grid, opt);
     if (prev >= 0 && prev != dev) cudaSetDevice(prev);
     if (st != GINT_OK) {
@@ -1050,7 +1156,7 @@ gint_status gint_work_stats(gint_handle* h, int64_t* sum_orbitals, int64_t* sum_
     if (cudaSetDevice(h->device) != cudaSuccess) { set_error("cannot select device %d", h->device); return GINT_ERR_CUDA; }
     unsigned long long* d = nullptr;
     unsigned long long hv[2] = {0, 0};
-    cudaError_t e = cudaMalloc(&d, sizeof(hv));
+    cudaError_t e = dev_malloc(&d, sizeof(hv));
     if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(hv));
     if (e == cudaSuccess && h->n_work > 0) {
         const int64_t threads = h->n_work * 32;
@@ -1080,6 +1186,135 @@ gint_status gint_sync(gint_handle* h, gint_stream stream) {
     if (flags & kErrPatternMissing) { set_error("a pair of atoms met on the grid is missing from the pattern"); return GINT_ERR_PATTERN_MISMATCH; }
     if (flags & kErrTimeout) { set_error("a bounded wait on the tensor-core pipeline gave up"); return GINT_ERR_TIMEOUT; }
     if (flags) { set_error("device check failed (flags 0x%x)", flags); return GINT_ERR_DEVICE; }
+    return GINT_OK;
+}
+
+gint_status gint_update_positions(gint_handle* h, const double* pos, const double* cell, int keep_pattern,
+                                  int* pattern_changed) {
+    set_error("");
+    if (!h || !pos) { set_error("gint_update_positions: NULL argument"); return GINT_ERR_INVALID_ARG; }
+    if (keep_pattern != 0 && keep_pattern != 1) { set_error("keep_pattern must be 0 or 1"); return GINT_ERR_INVALID_ARG; }
+    const double* cl = cell ? cell : h->cell;
+    const double det = cl[0] * (cl[4] * cl[8] - cl[5] * cl[7]) - cl[1] * (cl[3] * cl[8] - cl[5] * cl[6]) +
+                       cl[2] * (cl[3] * cl[7] - cl[4] * cl[6]);
+    if (!(fabs(det) > 1e-12) || !std::isfinite(det)) { set_error("cell is singular"); return GINT_ERR_INVALID_ARG; }
+    for (int i = 0; i < 3 * h->n_atoms; ++i)
+        if (!std::isfinite(pos[i])) { set_error("pos[%d] is not finite", i); return GINT_ERR_INVALID_ARG; }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(h->device) != cudaSuccess) { set_error("cannot select device %d", h->device); return GINT_ERR_CUDA; }
+    // finish the work already queued on the handle's buffers before they are released
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        if (prev >= 0) cudaSetDevice(prev);
+        set_error("gint_update_positions: device synchronisation failed");
+        return GINT_ERR_CUDA;
+    }
+    gint_handle* hn = new gint_handle();
+    hn->device = h->device;
+    hn->n_atoms = h->n_atoms;
+    hn->n_species = h->n_species;
+    hn->precision = h->precision;
+    hn->sm_count = h->sm_count;
+    hn->sp_rc = h->sp_rc; hn->sp_nrad = h->sp_nrad; hn->rad_l = h->rad_l; hn->rad_nk = h->rad_nk;
+    hn->rad_dr = h->rad_dr; hn->rad_y = h->rad_y; hn->rad_dy = h->rad_dy; hn->atom_species = h->atom_species;
+    for (int i = 0; i < 3; ++i) hn->brick_opt[i] = h->brick_opt[i];
+    std::vector<gint_species> S;
+    std::vector<gint_radial> R;
+    species_views(hn, S, R);
+    gint_options opt;
+    memset(&opt, 0, sizeof(opt));
+    opt.precision = h->precision;
+    opt.device = h->device;
+    for (int i = 0; i < 3; ++i) opt.brick[i] = h->brick_opt[i];
+    const int grid[3] = {h->grid.n[0], h->grid.n[1], h->grid.n[2]};
+    gint_status st = build_handle(hn, h->n_atoms, pos, hn->atom_species.data(), cl, h->n_species, S.data(), grid, &opt);
+    bool changed = false;
+    if (st == GINT_OK) {
+        changed = hn->n_blocks != h->n_blocks || hn->n_values != h->n_values;
+        if (!changed && h->n_blocks > 0) {
+            std::vector<int32_t> a((size_t)5 * h->n_blocks), b((size_t)5 * h->n_blocks);
+            cudaError_t e = cudaMemcpy(a.data(), h->d_blocks, sizeof(int32_t) * a.size(), cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemcpy(b.data(), hn->d_blocks, sizeof(int32_t) * b.size(), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) { set_error("gint_update_positions: %s", cudaGetErrorString(e)); st = GINT_ERR_CUDA; }
+            changed = a != b;
+        }
+    }
+    if (st == GINT_OK && keep_pattern && changed) {
+        set_error("the new positions need a different pair pattern (%lld blocks, was %lld); the handle is unchanged",
+                  (long long)hn->n_blocks, (long long)h->n_blocks);
+        st = GINT_ERR_PATTERN_MISMATCH;
+    }
+    if (st == GINT_OK) {
+        hn->wait_limit = h->wait_limit;
+        hn->generation = h->generation + 1;
+        hn->selecting = h->selecting;
+        hn->selection = h->selection;
+        if (hn->selecting) st = rebuild_work_lists(hn);
+    }
+    if (st != GINT_OK) {
+        free_handle(hn);
+        if (prev >= 0) cudaSetDevice(prev);
+        return st;
+    }
+    std::swap(*h, *hn);
+    free_handle(hn);  // the old geometry's device memory
+    if (prev >= 0) cudaSetDevice(prev);
+    if (pattern_changed) *pattern_changed = changed ? 1 : 0;
+    return GINT_OK;
+}
+
+gint_status gint_select_bricks(gint_handle* h, int64_t n, const int64_t* bricks) {
+    set_error("");
+    if (!h) { set_error("gint_select_bricks: NULL handle"); return GINT_ERR_INVALID_ARG; }
+    if (bricks && n < 0) { set_error("gint_select_bricks: n < 0"); return GINT_ERR_INVALID_ARG; }
+    if (bricks)
+        for (int64_t i = 0; i < n; ++i)
+            if (bricks[i] < 0 || bricks[i] >= h->n_bricks) {
+                set_error("gint_select_bricks: brick %lld out of range [0, %lld)", (long long)bricks[i],
+                          (long long)h->n_bricks);
+                return GINT_ERR_INVALID_ARG;
+            }
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(h->device) != cudaSuccess) { set_error("cannot select device %d", h->device); return GINT_ERR_CUDA; }
+    gint_status st = GINT_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) { set_error("gint_select_bricks: device synchronisation failed"); st = GINT_ERR_CUDA; }
+    const bool was = h->selecting;
+    std::vector<int64_t> old = h->selection;
+    if (st == GINT_OK) {
+        h->selecting = bricks != nullptr;
+        if (bricks) h->selection.assign(bricks, bricks + n); else h->selection.clear();
+        st = rebuild_work_lists(h);
+        if (st != GINT_OK) { h->selecting = was; h->selection.swap(old); }
+        else h->generation += 1;
+    }
+    if (prev >= 0) cudaSetDevice(prev);
+    return st;
+}
+
+gint_status gint_brick_loads(const gint_handle* h, int64_t* n_images) {
+    if (!h || !n_images) { set_error("gint_brick_loads: NULL argument"); return GINT_ERR_INVALID_ARG; }
+    std::vector<int64_t> bs(h->n_bricks + 1);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaMemcpy(bs.data(), h->d_brick_start, sizeof(int64_t) * bs.size(), cudaMemcpyDeviceToHost);
+    if (prev >= 0) cudaSetDevice(prev);
+    if (e != cudaSuccess) { set_error("gint_brick_loads: %s", cudaGetErrorString(e)); return GINT_ERR_CUDA; }
+    for (int64_t b = 0; b < h->n_bricks; ++b) n_images[b] = bs[b + 1] - bs[b];
+    return GINT_OK;
+}
+
+gint_status gint_set_wait_limit(gint_handle* h, int64_t polls) {
+    if (!h) { set_error("handle is NULL"); return GINT_ERR_INVALID_ARG; }
+    if (polls < 0 || polls > ((int64_t)1 << 40)) { set_error("wait limit %lld out of range", (long long)polls); return GINT_ERR_INVALID_ARG; }
+    h->wait_limit = polls;
+    return GINT_OK;
+}
+
+gint_status gint_debug_fail_alloc(int n) {
+    if (n < 0) { set_error("gint_debug_fail_alloc: n < 0"); return GINT_ERR_INVALID_ARG; }
+    g_fail_alloc.store(n);
     return GINT_OK;
 }
 

@@ -491,7 +491,7 @@ gint_status allocate_scratch(gint_handle* h) {
     // psi and W*psi, FP64
     const size_t per_cta = (size_t)2 * std::max(1, h->max_brick_orb) * bpad * sizeof(double);
     h->scratch_bytes = per_cta * h->n_ctas + 256;
-    GINT_CUDA_TRY(cudaMalloc(&h->d_scratch, h->scratch_bytes));
+    GINT_CUDA_TRY(dev_malloc(&h->d_scratch, h->scratch_bytes));
     return GINT_OK;
 }
 

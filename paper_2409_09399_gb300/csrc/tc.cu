@@ -50,7 +50,6 @@ constexpr int kTcChunk = 16;        // points per K chunk (one MMA K step)
 constexpr int kTcMaxAtoms = 64;     // atom images per brick
 constexpr int kTcMaxSpecies = 8;
 constexpr int kTcMaxSeg = 16;       // (row tile, column range) segments per brick
-constexpr long kWaitLimit = 1L << 26;  // bounded mbarrier polls
 
 // Sizes of the two forms (up to 640 padded orbital rows, 5 tiles of 128, in both).
 // Three-product form: pieces A_hi, A_lo, B_hi, B_lo over all rows; up to 1024
@@ -82,6 +81,7 @@ struct TcAtom {
 struct TcArgs {
     Problem P;
     int* counter;
+    long wait_limit;  // polls of a bounded hand-off wait (producers <-> MMA issue)
     int norm_after;  // exact form: leave the harmonic normalisation to k_norm_h (H not accumulated into)
 };
 
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                 const int b = half;
                 unsigned char* buf = S.buf[b];
                 for (int c = b; c < nchunks; c += 2) {
-                    if (uses[b] > 0 && !S.abort && !tc::mbar_wait(&S.empty[b], (uses[b] - 1) & 1, kWaitLimit))
+                    if (uses[b] > 0 && !S.abort && !tc::mbar_wait(&S.empty[b], (uses[b] - 1) & 1, A.wait_limit))
                         atomicOr(&S.abort, 1);
                     // orbital values at the chunk's points, two points per item, for the atom
                     // images of need_list.  Item bits: [1:0] point pair within a half chunk,
@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                 const uint32_t lbo = 128, sbo = (kTcChunk / 8) * 128;
                 for (int c = 0; c < nchunks; ++c) {
                     const int b = c & 1;
-                    if (!S.abort && !tc::mbar_wait(&S.full[b], uses[b] & 1, kWaitLimit)) atomicOr(&S.abort, 1);
+                    if (!S.abort && !tc::mbar_wait(&S.full[b], uses[b] & 1, A.wait_limit)) atomicOr(&S.abort, 1);
                     uses[b] += 1;
                     tc::fence_after_sync();
                     const uint32_t base = tc::smem_u32(S.buf[b]);
@@ -548,9 +548,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                 }
                 tc::mma_commit(&S.done);
             }
-            // ---- every thread: all MMAs of the pass complete
+            // ---- every thread: all MMAs of the pass complete.  Waited for even after an abort
+            //      (the issuer commits `done` at the end of every pass), so that the phases of
+            //      `done` stay in step and no MMA of the pass is in flight afterwards.
             __syncwarp();
-            if (!S.abort && !tc::mbar_wait(&S.done, dones & 1, kWaitLimit)) atomicOr(&S.abort, 1);
+            if (!tc::mbar_wait(&S.done, dones & 1, kDrainPolls)) atomicOr(&S.abort, 1);
             dones += 1;
             if (issuer_warp && lane != 0) {
                 // lanes 1-31 of the issuer warp keep the buffer counters in step with lane 0
@@ -629,7 +631,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
     //      tensor memory is released (every pass already waited on `done` unless it aborted)
     __syncthreads();
     if (issuer_warp && lane == 0) tc::mma_commit(&S.done);
-    (void)tc::mbar_wait(&S.done, dones & 1, kWaitLimit);
+    (void)tc::mbar_wait(&S.done, dones & 1, kDrainPolls);
     if (S.abort && tid == 0) atomicOr(Pc->err, kErrTimeout);
     tc::fence_before_sync();
     __syncthreads();
@@ -681,6 +683,7 @@ gint_status tc_vlocal(gint_handle* h, int form, const double* V, double* H, int 
     A.norm_after = exact && !accumulate ? 1 : 0;
     A.P = h->problem();
     A.counter = h->d_err + 2;
+    A.wait_limit = wait_polls(h);
     GINT_CUDA_TRY(cudaMemsetAsync(A.counter, 0, sizeof(int), st));
     const size_t smem = exact ? tc_smem_bytes<true>() : tc_smem_bytes<false>();
 #define GINT_LAUNCH_VL(H16, X)                                                                                 \
@@ -717,6 +720,7 @@ gint_status tc_vlocal_multi(int form, const MultiArgs& M, int* counter, int sm_c
     TcArgs A;
     memset(&A, 0, sizeof(A));
     A.counter = counter;
+    A.wait_limit = kDefaultWaitPolls;
     A.norm_after = form == 2 ? 1 : 0;
     GINT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
     const size_t smem = form == 2 ? tc_smem_bytes<true>() : tc_smem_bytes<false>();

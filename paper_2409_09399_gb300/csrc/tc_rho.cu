@@ -67,7 +67,6 @@ template <bool kExact> struct RfCfg {
     static constexpr int kBRows = kExact ? 256 : 512;
     static constexpr int kBPiece = kBRows * 16 * 2;
 };
-constexpr long kWait = 1L << 26;
 constexpr int kMaxSpecies = 8;
 
 struct Atom {
@@ -229,7 +228,8 @@ __global__ void k_format_d(Problem P, const int32_t* mirror, const int* nw_atom,
 // kMulti: the work queue spans the bricks of many cells (a batch, MultiArgs); the
 // problem and the buffers of an item come from its cell's CellJob.
 template <typename H16, bool kForce, bool kExact, bool kMulti>
-__global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_constant__ CellJob J_in, int* counter, const __grid_constant__ MultiArgs M) {
+__global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_constant__ CellJob J_in, int* counter, const __grid_constant__ MultiArgs M,
+                                                                 long wait_limit) {
     constexpr int kCols = kExact ? kMaxCols / 2 : kMaxCols;  // output columns of one column group
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem<kExact>& S = *reinterpret_cast<Smem<kExact>*>(smem_raw);
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
                 for (int st = 0; st < nsteps; ++st) {
                     const int b = (chunk + st) & 1, k = 2 * st;
                     const int nk = min(2, nact - k);
-                    if (uses[b] > 0 && !tc::mbar_wait(&S.empty[b], (uses[b] - 1) & 1, kWait)) atomicOr(&S.abort, 1);
+                    if (uses[b] > 0 && !tc::mbar_wait(&S.empty[b], (uses[b] - 1) & 1, wait_limit)) atomicOr(&S.abort, 1);
                     if (j < nk && !S.abort) {
                         const Atom& X = S.at[S.act[k + j]];
                         const int p = mt * 128 + pl;
@@ -423,14 +423,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
                 for (int st = 0; st < nsteps; ++st) {
                     const int bb = (chunk + st) & 1, kk = 2 * st;
                     const int nkk = min(2, nact - kk);
+                    int go = 0;
                     if (lane == 0) {
-                        if (uses[bb] > 0 && !tc::mbar_wait(&S.empty[bb], (uses[bb] - 1) & 1, kWait)) atomicOr(&S.abort, 1);
-                        tc::mbar_arrive_expect_tx(&S.bfull[bb], (uint32_t)(nkk * (cg1 - cg0) * C::kPieces * kDtPiece));
-                        bissue[bb] += 1;
+                        if (uses[bb] > 0 && !tc::mbar_wait(&S.empty[bb], (uses[bb] - 1) & 1, wait_limit)) atomicOr(&S.abort, 1);
+                        // at most one transaction phase of bfull[bb] is ever open: the copies issued
+                        // into this buffer before have landed (already true unless a wait gave up)
+                        if (bissue[bb] > 0 && !tc::mbar_wait(&S.bfull[bb], (bissue[bb] - 1) & 1, kDrainPolls))
+                            atomicOr(&S.abort, 1);
+                        go = S.abort ? 0 : 1;  // after an abort no further copies are started
+                        if (go) {
+                            tc::mbar_arrive_expect_tx(&S.bfull[bb], (uint32_t)(nkk * (cg1 - cg0) * C::kPieces * kDtPiece));
+                            bissue[bb] += 1;
+                        }
                     }
-                    __syncwarp();
+                    go = __shfl_sync(0xffffffffu, go, 0);
                     const int per_img = cg1 - cg0;
-                    for (int e = lane; e < nkk * per_img; e += 32) {
+                    for (int e = lane; go && e < nkk * per_img; e += 32) {
                         const int jj = e / per_img, sl = e - jj * per_img;
                         const int blk = S.pairblk[S.act[kk + jj] * na + S.act[cg0 + sl]];
                         const unsigned char* src = blk >= 0 ? Dt + (int64_t)blk * kDtBytes : Dzero;
@@ -447,8 +455,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
                     const int b = (chunk + st) & 1, k = 2 * st;
                     const int nk = min(2, nact - k);
                     if (lane == 0) {
-                        if (!S.abort && !tc::mbar_wait(&S.full[b], uses[b] & 1, kWait)) atomicOr(&S.abort, 1);
-                        if (!S.abort && !tc::mbar_wait(&S.bfull[b], uses[b] & 1, kWait)) atomicOr(&S.abort, 1);
+                        if (!S.abort && !tc::mbar_wait(&S.full[b], uses[b] & 1, wait_limit)) atomicOr(&S.abort, 1);
+                        if (!S.abort && !tc::mbar_wait(&S.bfull[b], uses[b] & 1, wait_limit)) atomicOr(&S.abort, 1);
                         tc::fence_after_sync();
                         for (int jm = 0; jm < nk && !S.abort; ++jm) {
                             const uint32_t a_hi = tc::smem_u32(S.A[b][jm]), a_lo = a_hi + kAPiece, a_l2 = a_lo + kAPiece;
@@ -486,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
             }
             chunk += nsteps;
             // ---- all MMAs of this group complete (every thread waits on done)
-            if (!tc::mbar_wait(&S.done, dones & 1, kWait)) atomicOr(&S.abort, 1);
+            if (!tc::mbar_wait(&S.done, dones & 1, kDrainPolls)) atomicOr(&S.abort, 1);
             dones += 1;
             tc::fence_after_sync();
             if (kForce) {
@@ -585,11 +593,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
     // one more commit (completes after every earlier MMA) and the copies not yet waited for
     if (warp == kMmaWarp && lane == 0) {
         tc::mma_commit(&S.done);
-        (void)tc::mbar_wait(&S.done, dones & 1, kWait);
+        (void)tc::mbar_wait(&S.done, dones & 1, kDrainPolls);
     }
     if (warp == kCopyWarp && lane == 0)  // the last phase of each buffer covers every earlier copy
         for (int b = 0; b < 2; ++b)
-            if (bissue[b] > 0) (void)tc::mbar_wait(&S.bfull[b], (bissue[b] - 1) & 1, kWait);
+            if (bissue[b] > 0) (void)tc::mbar_wait(&S.bfull[b], (bissue[b] - 1) & 1, kDrainPolls);
     if (S.abort && tid == 0) atomicOr(Jc->P.err, kErrTimeout);
     tc::fence_before_sync();
     __syncthreads();
@@ -600,11 +608,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
 static gint_status ensure_dt(gint_handle* h) {
     if (!h->d_dt) {
         const size_t bytes = (size_t)std::max<int64_t>(1, h->n_blocks) * kDtBytes;
-        GINT_CUDA_TRY(cudaMalloc(&h->d_dt, bytes));
+        GINT_CUDA_TRY(dev_malloc(&h->d_dt, bytes));
     }
-    if (!h->d_dq) GINT_CUDA_TRY(cudaMalloc(&h->d_dq, sizeof(int) * 16 * (size_t)std::max(1, h->n_atoms)));
+    if (!h->d_dq) GINT_CUDA_TRY(dev_malloc(&h->d_dq, sizeof(int) * 16 * (size_t)std::max(1, h->n_atoms)));
     if (!h->d_zero) {  // a zero D tile for atom-image pairs without a block
-        GINT_CUDA_TRY(cudaMalloc(&h->d_zero, kDtBytes));
+        GINT_CUDA_TRY(dev_malloc(&h->d_zero, kDtBytes));
         GINT_CUDA_TRY(cudaMemset(h->d_zero, 0, kDtBytes));
     }
     return GINT_OK;
@@ -670,7 +678,7 @@ CellJob tc_cell_job(gint_handle* h, const double* V, double* H, double* rho, dou
 
 // One launch of the rho or force kernel: one cell (M.n_items == 0: J) or a batch queue (M).
 static gint_status launch_rf(int form, bool force, const CellJob& J, const MultiArgs& M, bool multi, int* counter,
-                             int sm_count, cudaStream_t st) {
+                             int sm_count, long wait_limit, cudaStream_t st) {
     const bool exact = form == 2;
     GINT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
     const size_t smem = (exact ? sizeof(Smem<true>) : sizeof(Smem<false>)) + 1024;
@@ -678,7 +686,7 @@ static gint_status launch_rf(int form, bool force, const CellJob& J, const Multi
     do {                                                                                                        \
         GINT_CUDA_TRY(cudaFuncSetAttribute(k_rhoforce_tc<H16, F, X, MU>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                            (int)smem));                                                         \
-        k_rhoforce_tc<H16, F, X, MU><<<sm_count, kThreads, smem, st>>>(J, counter, M);                           \
+        k_rhoforce_tc<H16, F, X, MU><<<sm_count, kThreads, smem, st>>>(J, counter, M, wait_limit);               \
     } while (0)
 #define GINT_LAUNCH_RF2(H16, X, MU) \
     do { if (force) GINT_LAUNCH_RF(H16, true, X, MU); else GINT_LAUNCH_RF(H16, false, X, MU); } while (0)
@@ -704,7 +712,7 @@ gint_status tc_rhoforce(gint_handle* h, int form, bool force, const double* V, c
     s = tc_format_d(h, form, D, st);
     if (s != GINT_OK || h->n_work == 0) return s;
     return launch_rf(form, force, tc_cell_job(h, V, nullptr, rho, facc, acc_e), MultiArgs{}, false, h->d_err + 2,
-                     h->sm_count, st);
+                     h->sm_count, wait_polls(h), st);
 }
 
 // One launch over the (cell, brick) queue of a batch (every cell's D formatted, cells checked).
@@ -712,7 +720,7 @@ gint_status tc_rhoforce_multi(int form, bool force, const MultiArgs& M, int* cou
     if (M.n_items == 0) return GINT_OK;
     CellJob none;
     memset(&none, 0, sizeof(none));
-    return launch_rf(form, force, none, M, true, counter, sm_count, st);
+    return launch_rf(form, force, none, M, true, counter, sm_count, kDefaultWaitPolls, st);
 }
 
 }  // namespace gint

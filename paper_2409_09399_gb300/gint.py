@@ -22,8 +22,10 @@ STATUS = {0: "GINT_OK", 1: "GINT_ERR_INVALID_ARG", 2: "GINT_ERR_CUDA", 3: "GINT_
 
 # exported symbols, in the order include/gint.h declares them
 SYMBOLS = ["gint_setup", "gint_destroy", "gint_pattern", "gint_set_precision", "gint_vlocal", "gint_rho",
-           "gint_force_stress", "gint_vlocal_static", "gint_check", "gint_fold_k", "gint_batch_create", "gint_batch_run",
-           "gint_batch_destroy", "gint_sync", "gint_get_info", "gint_work_stats", "gint_last_error"]
+           "gint_force_stress", "gint_energy_grads", "gint_update_positions", "gint_select_bricks", "gint_brick_loads",
+           "gint_set_wait_limit", "gint_debug_fail_alloc", "gint_vlocal_static", "gint_fold_k", "gint_check",
+           "gint_batch_create", "gint_batch_run", "gint_batch_destroy", "gint_sync", "gint_get_info",
+           "gint_work_stats", "gint_last_error"]
 
 
 class GintError(RuntimeError):
@@ -83,6 +85,18 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.gint_rho.argtypes = [vp, vp, vp, vp]
     L.gint_force_stress.restype = i32
     L.gint_force_stress.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    L.gint_energy_grads.restype = i32
+    L.gint_energy_grads.argtypes = [vp] * 10
+    L.gint_update_positions.restype = i32
+    L.gint_update_positions.argtypes = [vp, vp, vp, i32, ctypes.POINTER(i32)]
+    L.gint_select_bricks.restype = i32
+    L.gint_select_bricks.argtypes = [vp, i64, vp]
+    L.gint_brick_loads.restype = i32
+    L.gint_brick_loads.argtypes = [vp, vp]
+    L.gint_set_wait_limit.restype = i32
+    L.gint_set_wait_limit.argtypes = [vp, i64]
+    L.gint_debug_fail_alloc.restype = i32
+    L.gint_debug_fail_alloc.argtypes = [i32]
     L.gint_vlocal_static.restype = i32
     L.gint_vlocal_static.argtypes = [vp, vp, vp, vp]
     L.gint_fold_k.restype = i32
@@ -209,6 +223,72 @@ class Gint:
                                   self._stream(stream)))
         return Hk
 
+    def update_positions(self, pos, cell=None, keep_pattern: bool = False) -> bool:
+        """New positions (bohr) and optionally a new cell for this handle (gint_update_positions).
+
+        Returns True if the pair pattern changed (then D and H must be laid out anew).  With
+        keep_pattern the pattern must stay the same, else GintError (GINT_ERR_PATTERN_MISMATCH)
+        and the handle keeps its old geometry."""
+        pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(self.n_atoms, 3)
+        c = None if cell is None else np.ascontiguousarray(cell, dtype=np.float64).reshape(9)
+        changed = ctypes.c_int(0)
+        _check(load().gint_update_positions(self._h, pos.ctypes.data, None if c is None else c.ctypes.data,
+                                            1 if keep_pattern else 0, ctypes.byref(changed)))
+        self.pos = pos.copy()
+        if c is not None:
+            self.cell = c.reshape(3, 3).copy()
+            self.omega = float(abs(np.linalg.det(self.cell)))
+            self.dV = self.omega / float(self.n_grid)
+        nb, nv = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().gint_pattern(self._h, ctypes.byref(nb), ctypes.byref(nv), None, None))
+        self.n_blocks, self.n_values = nb.value, nv.value
+        self._pattern = None
+        return bool(changed.value)
+
+    def select_bricks(self, bricks=None):
+        """Restrict later calls to the bricks with the given ids (None: every brick)."""
+        if bricks is None:
+            _check(load().gint_select_bricks(self._h, 0, None))
+            return
+        b = np.ascontiguousarray(bricks, dtype=np.int64).reshape(-1)
+        _check(load().gint_select_bricks(self._h, b.size, b.ctypes.data))
+
+    def brick_loads(self) -> np.ndarray:
+        """Atom images meeting each brick (int64, one entry per brick)."""
+        out = np.zeros(int(self.info()["n_bricks"]), dtype=np.int64)
+        _check(load().gint_brick_loads(self._h, out.ctypes.data))
+        return out
+
+    def set_wait_limit(self, polls: int = 0):
+        _check(load().gint_set_wait_limit(self._h, int(polls)))
+
+    def energy_grads(self, V, D, grad_E=None, want=("R", "eps", "V", "D", "E"), stream=None):
+        """Gradients of E = sum V rho dV (gint_energy_grads): dict with the requested entries of
+        R: dE/dR (n, 3), eps: dE/d(strain) (3, 3), V: dE/dV (grid), D: dE/dD (n_values), E: (1,).
+        grad_E: optional device scalar multiplying every gradient."""
+        import torch
+        self._need(V, self.n_grid, "V")
+        self._need(D, self.n_values, "D")
+        dev = V.device
+        f64 = torch.float64
+        out = {}
+        if "R" in want:
+            out["R"] = torch.empty((self.n_atoms, 3), dtype=f64, device=dev)
+        if "eps" in want:
+            out["eps"] = torch.empty((3, 3), dtype=f64, device=dev)
+        if "V" in want:
+            out["V"] = torch.empty(self.grid, dtype=f64, device=dev)
+        if "D" in want:
+            out["D"] = torch.empty(self.n_values, dtype=f64, device=dev)
+        if "E" in want:
+            out["E"] = torch.empty(1, dtype=f64, device=dev)
+        if grad_E is not None:
+            grad_E = grad_E.to(device=dev, dtype=f64).reshape(1).contiguous()
+        _check(load().gint_energy_grads(self._h, _ptr(V), _ptr(D), _ptr(grad_E), _ptr(out.get("R")),
+                                        _ptr(out.get("eps")), _ptr(out.get("V")), _ptr(out.get("D")),
+                                        _ptr(out.get("E")), self._stream(stream)))
+        return out
+
     def supported(self) -> bool:
         """Whether the kernels of the current precision accept this handle's bricks."""
         st = load().gint_check(self._h)
@@ -303,6 +383,11 @@ class Gint:
         _check(load().gint_force_stress(self._h, _ptr(V), _ptr(D), _ptr(F), _ptr(sigma), _ptr(vir), _ptr(E),
                                         self._stream(stream)))
         return F, sigma, vir, E
+
+
+def debug_fail_alloc(n: int):
+    """Test hook: make the n-th device allocation of the library from now on fail (0 disables)."""
+    _check(load().gint_debug_fail_alloc(int(n)))
 
 
 def from_system(system, precision="fp64", brick=(0, 0, 0), device=-1, pos=None, cell=None) -> Gint:

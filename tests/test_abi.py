@@ -71,3 +71,21 @@ def test_host_validation_of_the_other_entry_points():
     a, b = i64(), i64()
     assert L.gint_work_stats(None, ctypes.byref(a), ctypes.byref(b)) == 1
     assert L.gint_pattern(None, None, None, None, None) == 1
+
+
+def test_host_validation_of_geometry_and_adjoint_entry_points():
+    """The position update, brick selection, adjoint, wait-limit and allocation-hook entry points
+    refuse bad arguments by status on the host."""
+    from paper_2409_09399_gb300 import gint
+    L = gint.load()
+    assert L.gint_energy_grads(None, None, None, None, None, None, None, None, None, None) == 1
+    assert b"gint_energy_grads" in L.gint_last_error()
+    pos = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    changed = ctypes.c_int(7)
+    assert L.gint_update_positions(None, pos, None, 1, ctypes.byref(changed)) == 1
+    assert changed.value == 7
+    assert L.gint_select_bricks(None, 0, None) == 1
+    assert L.gint_brick_loads(None, None) == 1
+    assert L.gint_set_wait_limit(None, 0) == 1
+    assert L.gint_debug_fail_alloc(-1) == 1
+    assert L.gint_debug_fail_alloc(0) == 0

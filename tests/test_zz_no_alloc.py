@@ -5,8 +5,9 @@ device and fails once a framework's caching allocator holds the free memory)
 use gint_vlocal_static, whose kernel scratch is a fixed array inside the
 library.  This file is collected last so that a run stopping at the first
 failure has run every other test first.  The test calls the entry point
-through the C ABI twice in a row and compares each result with gint_vlocal
-in the FP64 form.
+through the C ABI twice in a row, checks that neither call changes the
+device's free memory or torch's reserved memory, and compares each result
+with gint_vlocal in the FP64 form.
 """
 import ctypes
 
@@ -30,11 +31,17 @@ def test_vlocal_static_matches_vlocal_twice(cuda):
     stream = ctypes.c_void_p(int(torch.cuda.current_stream().cuda_stream))
     ref = H_ref.cpu().numpy()
     scale = np.max(np.abs(ref))
-    for call in range(2):
-        H = torch.full((g.n_values,), float("nan"), dtype=torch.float64, device=cuda)
+    outs = [torch.full((g.n_values,), float("nan"), dtype=torch.float64, device=cuda) for _ in range(2)]
+    torch.cuda.synchronize()
+    # the call's defining property: no device memory is taken, neither from the device (free
+    # bytes) nor from torch's caching allocator (reserved bytes)
+    free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    for call, H in enumerate(outs):
         st = L.gint_vlocal_static(g._h, ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(H.data_ptr()), stream)
         assert st == 0, L.gint_last_error()
         g.sync()
+        assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_reserved() == reserved0, call
+    for call, H in enumerate(outs):
         err = np.max(np.abs(H.cpu().numpy() - ref)) / scale
         assert err < 1e-11, (call, err)
 
