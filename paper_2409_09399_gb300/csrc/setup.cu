@@ -580,7 +580,14 @@ static gint_status dev_upload(T** dst, const T* src, size_t n) {
     *dst = nullptr;
     if (n == 0) n = 1;
     GINT_CUDA_TRY(dev_malloc((void**)dst, sizeof(T) * n));
-    if (src) GINT_CUDA_TRY(cudaMemcpy(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice));
+    if (src) {
+        const cudaError_t e = cudaMemcpy(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(*dst);
+            *dst = nullptr;
+            GINT_CUDA_TRY(e);
+        }
+    }
     return GINT_OK;
 }
 
@@ -727,22 +734,26 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
     int* d_spc = nullptr;
     double* d_rc = nullptr;
     int* d_nw = nullptr;
-    GINT_TRY(dev_upload(&d_pos, pos, (size_t)3 * n_atoms));
-    GINT_TRY(dev_upload(&d_spc, spc.data(), spc.size()));
-    GINT_TRY(dev_upload(&d_rc, rc_sp.data(), rc_sp.size()));
-    GINT_TRY(dev_upload(&d_nw, nw_sp.data(), nw_sp.size()));
+    // temporaries of the set-up, released on every return (each is listed as soon as it exists)
     struct Tmp {
         std::vector<void*> p;
         ~Tmp() { for (void* x : p) cudaFree(x); }
     } tmp;
-    tmp.p = {d_pos, d_spc, d_rc, d_nw};
+    GINT_TRY(dev_upload(&d_pos, pos, (size_t)3 * n_atoms));
+    tmp.p.push_back(d_pos);
+    GINT_TRY(dev_upload(&d_spc, spc.data(), spc.size()));
+    tmp.p.push_back(d_spc);
+    GINT_TRY(dev_upload(&d_rc, rc_sp.data(), rc_sp.size()));
+    tmp.p.push_back(d_rc);
+    GINT_TRY(dev_upload(&d_nw, nw_sp.data(), nw_sp.size()));
+    tmp.p.push_back(d_nw);
     cudaStream_t st = 0;
 
     // ---- pattern (Section 2.2 sparsity): rows I, sorted (J, t)
     int64_t *d_rc_cnt = nullptr, *d_rv = nullptr;
     GINT_CUDA_TRY(dev_malloc(&d_rc_cnt, sizeof(int64_t) * (n_atoms + 1)));
-    GINT_CUDA_TRY(dev_malloc(&d_rv, sizeof(int64_t) * (n_atoms + 1)));
     tmp.p.push_back(d_rc_cnt);
+    GINT_CUDA_TRY(dev_malloc(&d_rv, sizeof(int64_t) * (n_atoms + 1)));
     tmp.p.push_back(d_rv);
     k_pattern_count<<<n_atoms, 256, 0, st>>>(c, n_atoms, d_pos, d_spc, d_rc, d_nw, d_rc_cnt, d_rv);
     GINT_CUDA_TRY(cudaGetLastError());
@@ -820,8 +831,8 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
     int64_t nbk = h->n_bricks;
     int64_t *d_count = nullptr, *d_fill = nullptr;
     GINT_CUDA_TRY(dev_malloc(&d_count, sizeof(int64_t) * (nbk + 1)));
-    GINT_CUDA_TRY(dev_malloc(&d_fill, sizeof(int64_t) * (nbk + 1)));
     tmp.p.push_back(d_count);
+    GINT_CUDA_TRY(dev_malloc(&d_fill, sizeof(int64_t) * (nbk + 1)));
     tmp.p.push_back(d_fill);
     GINT_CUDA_TRY(cudaMemset(d_count, 0, sizeof(int64_t) * (nbk + 1)));
     GINT_CUDA_TRY(cudaMemset(d_fill, 0, sizeof(int64_t) * (nbk + 1)));
@@ -848,14 +859,14 @@ static gint_status build_handle(gint_handle* h, int n_atoms, const double* pos, 
     int* d_max = nullptr;
     unsigned long long* d_sum = nullptr;
     GINT_CUDA_TRY(dev_malloc(&d_flag, sizeof(int64_t) * (nbk + 1)));
-    GINT_CUDA_TRY(dev_malloc(&d_pairs, sizeof(int64_t) * (nbk + 1)));
-    GINT_CUDA_TRY(dev_malloc(&d_pos_ne, sizeof(int64_t) * (nbk + 1)));
-    GINT_CUDA_TRY(dev_malloc(&d_max, sizeof(int) * 2));
-    GINT_CUDA_TRY(dev_malloc(&d_sum, sizeof(unsigned long long)));
     tmp.p.push_back(d_flag);
+    GINT_CUDA_TRY(dev_malloc(&d_pairs, sizeof(int64_t) * (nbk + 1)));
     tmp.p.push_back(d_pairs);
+    GINT_CUDA_TRY(dev_malloc(&d_pos_ne, sizeof(int64_t) * (nbk + 1)));
     tmp.p.push_back(d_pos_ne);
+    GINT_CUDA_TRY(dev_malloc(&d_max, sizeof(int) * 2));
     tmp.p.push_back(d_max);
+    GINT_CUDA_TRY(dev_malloc(&d_sum, sizeof(unsigned long long)));
     tmp.p.push_back(d_sum);
     GINT_CUDA_TRY(cudaMemset(d_max, 0, sizeof(int) * 2));
     GINT_CUDA_TRY(cudaMemset(d_sum, 0, sizeof(unsigned long long)));
