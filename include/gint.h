@@ -227,6 +227,26 @@ gint_status gint_set_wait_limit(gint_handle* h, int64_t polls);
  * released everything it allocated. */
 gint_status gint_debug_fail_alloc(int n);
 
+/* The local potential from rho, the step of Fig. 1 that precedes the grid integrals (Section
+ * 2.2, the text after Eq. 2: V is the sum of the local pseudopotentials, the Hartree and the
+ * exchange-correlation potentials):
+ *   V_out = V_ext + V_H + v_xc,
+ *   V_H:  periodic solution of lap V_H = -4 pi (rho - mean rho) on the handle's grid and cell,
+ *         V_H(G) = 4 pi rho(G) / |G|^2 with V_H(G = 0) = 0 (on the Nyquist index of an even axis
+ *         the kernel is the mean over G and -G, which keeps V_H real);
+ *   v_xc: LDA, Slater exchange + Perdew-Zunger (1981) correlation, spin unpolarised, in hartree;
+ *         0 where rho <= 0;
+ *   energies[0] = E_H = 1/2 sum_g rho_g V_H,g dV, energies[1] = E_xc = sum_g rho_g eps_xc,g dV.
+ * rho, V_ext, V_out, V_H: device grid arrays [n1][n2][n3] float64; V_ext may be NULL (zero);
+ * V_H may be NULL (not returned) and otherwise must not alias rho; V_out must not alias rho;
+ * energies: device double[2] or NULL.  rho is read only.  The two 3-D FFTs are cuFFT's,
+ * loaded at run time (GINT_ERR_UNSUPPORTED if libcufft cannot be loaded); the first call on a
+ * handle makes the FFT plans and a half-spectrum buffer (16 (n1 n2 (n3/2 + 1)) bytes), so make
+ * it before any stream capture.  Asynchronous on `stream`; grids above 2^31 points are
+ * GINT_ERR_UNSUPPORTED.  The brick selection does not apply (the whole grid is used). */
+gint_status gint_local_potential(gint_handle* h, const double* rho, const double* V_ext, double* V_out, double* V_H,
+                                 double* energies, gint_stream stream);
+
 /* H^V in the FP64 form, like gint_vlocal(h, V, H, 0, stream), without any
  * device allocation.  For callers that cannot let a library call cudaMalloc
  * (it synchronises the device and fails once a framework's caching allocator

@@ -10,6 +10,7 @@ sorted lexicographically, each block row-major nw_I x nw_J) and exposes:
   rho(D) / rho_points(D, g) -> density on the grid / at points   (Eq. 3)
   force(V, D, atoms)        -> F_I and per-atom virial Pi_I      (Eq. 4, 5)
   energy(V, D)              -> sum_g V rho dV
+  vlocal_masked / force_masked -> the same sums over a subset (shard) of the grid points
 """
 from __future__ import annotations
 
@@ -65,6 +66,9 @@ def lib():
         L.orc_rho_points.argtypes = [vp, _f64p, ctypes.c_int64, _i64p, _f64p]
         L.orc_energy.argtypes = [vp, _f64p, _f64p, ctypes.POINTER(ctypes.c_double)]
         L.orc_force.argtypes = [vp, _f64p, _f64p, ctypes.c_int, _i32p, _f64p, _f64p]
+        _u8p = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+        L.orc_vlocal_masked.argtypes = [vp, _f64p, _u8p, _f64p]
+        L.orc_force_masked.argtypes = [vp, _f64p, _f64p, _u8p, ctypes.c_int, _i32p, _f64p, _f64p]
         L.orc_eval_orbitals.argtypes = [vp, ctypes.c_int, ctypes.c_int64, _f64p, _f64p, _f64p]
         L.orc_num_threads.restype = ctypes.c_int
         _lib = L
@@ -210,6 +214,29 @@ class Oracle:
             ph = np.exp(2j * np.pi * float(kf @ t))
             Hk[off[I]:off[I + 1], off[J]:off[J + 1]] += ph * self.block(H, b)
         return Hk
+
+    def vlocal_masked(self, V, mask):
+        """H^V summed over the grid points with mask != 0 only (mask: bool/uint8 grid array)."""
+        V = np.ascontiguousarray(V, dtype=np.float64).reshape(-1)
+        m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+        H = np.zeros(self.n_values, dtype=np.float64)
+        if self.n_values:
+            lib().orc_vlocal_masked(self._h, V, m, H)
+        return H
+
+    def force_masked(self, V, D, mask, atoms=None):
+        """(F, per-atom virial) summed over the grid points with mask != 0 only."""
+        V = np.ascontiguousarray(V, dtype=np.float64).reshape(-1)
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+        if atoms is None:
+            atoms = np.arange(self.pos.shape[0])
+        atoms = np.ascontiguousarray(atoms, dtype=np.int32)
+        F = np.zeros((atoms.size, 3), dtype=np.float64)
+        W = np.zeros((atoms.size, 9), dtype=np.float64)
+        if lib().orc_force_masked(self._h, V, D, m, atoms.size, atoms, F.reshape(-1), W.reshape(-1)) != 0:
+            raise RuntimeError("oracle force: neighbour pair missing from the pattern")
+        return F, W.reshape(-1, 3, 3)
 
     def stress(self, V, D):
         F, W = self.force(V, D)

@@ -421,7 +421,13 @@ static void grid_box(const orc_ctx* c, const double p[3], double rad, int64_t lo
 }
 
 /* ------------------------------------------------------------- H^V (Eq. 2) */
-static void h_block(const orc_ctx* c, const double* V, int64_t b, double* out) {
+/* home index of grid point k (infinite space) in the cell's grid, C order */
+static inline int64_t home_index(const orc_ctx* c, const int64_t k[3]) {
+    return (pmod(k[0], c->n[0]) * c->n[1] + pmod(k[1], c->n[1])) * c->n[2] + pmod(k[2], c->n[2]);
+}
+
+/* mask (nullable): only grid points whose home index g has mask[g] != 0 enter the sum */
+static void h_block(const orc_ctx* c, const double* V, int64_t b, double* out, const unsigned char* mask) {
     int64_t I = c->blocks[5 * b], J = c->blocks[5 * b + 1];
     int64_t T[3] = {c->blocks[5 * b + 2], c->blocks[5 * b + 3], c->blocks[5 * b + 4]};
     const orc_species* SI = &c->species[c->sp[I]];
@@ -440,6 +446,7 @@ static void h_block(const orc_ctx* c, const double* V, int64_t b, double* out) {
         for (int64_t k1 = lo[1]; k1 <= hi[1]; ++k1)
             for (int64_t k2 = lo[2]; k2 <= hi[2]; ++k2) {
                 int64_t k[3] = {k0, k1, k2};
+                if (mask && !mask[home_index(c, k)]) continue;
                 double r[3], dI[3], dJ[3];
                 grid_point(c, k, r);
                 for (int j = 0; j < 3; ++j) { dI[j] = r[j] - RI[j]; dJ[j] = r[j] - RJ[j]; }
@@ -458,7 +465,14 @@ static void h_block(const orc_ctx* c, const double* V, int64_t b, double* out) {
 /* Full H on the oracle's own pattern and layout. */
 void orc_vlocal(const orc_ctx* c, const double* V, double* H) {
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int64_t b = 0; b < c->n_blocks; ++b) h_block(c, V, b, H + c->offsets[b]);
+    for (int64_t b = 0; b < c->n_blocks; ++b) h_block(c, V, b, H + c->offsets[b], NULL);
+}
+
+/* H restricted to the grid points with mask[g] != 0 (a shard of the grid): the sum of Eq. 2
+   over those points only, so that the shards of a partition of the grid add up to H. */
+void orc_vlocal_masked(const orc_ctx* c, const double* V, const unsigned char* mask, double* H) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t b = 0; b < c->n_blocks; ++b) h_block(c, V, b, H + c->offsets[b], mask);
 }
 
 /* Selected blocks (rows of sel: I, J, t1, t2, t3), written back to back.
@@ -473,7 +487,7 @@ int orc_vlocal_blocks(const orc_ctx* c, const double* V, int64_t n_sel, const in
         pos[q + 1] = pos[q] + (c->offsets[idx[q] + 1] - c->offsets[idx[q]]);
     }
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int64_t q = 0; q < n_sel; ++q) h_block(c, V, idx[q], out + pos[q]);
+    for (int64_t q = 0; q < n_sel; ++q) h_block(c, V, idx[q], out + pos[q], NULL);
     free(idx);
     free(pos);
     return 0;
@@ -599,8 +613,8 @@ int orc_energy(const orc_ctx* c, const double* V, const double* D, double* E) {
    Sum over grid points in infinite space within rc_I of R_I; parallel over
    the first grid index with per-slice compensated partial sums that are
    added in slice order, so the result does not depend on the thread count. */
-int orc_force(const orc_ctx* c, const double* V, const double* D, int n_sel, const int* atoms,
-              double* F, double* virial) {
+static int force_impl(const orc_ctx* c, const double* V, const double* D, int n_sel, const int* atoms,
+                      double* F, double* virial, const unsigned char* mask) {
     int err = 0;
     for (int q = 0; q < n_sel; ++q) {
         int I = atoms[q];
@@ -622,6 +636,7 @@ int orc_force(const orc_ctx* c, const double* V, const double* D, int n_sel, con
                 for (int64_t k1 = lo[1]; k1 <= hi[1]; ++k1)
                     for (int64_t k2 = lo[2]; k2 <= hi[2]; ++k2) {
                         int64_t k[3] = {k0, k1, k2};
+                        if (mask && !mask[home_index(c, k)]) continue;
                         double r[3], d[3];
                         grid_point(c, k, r);
                         for (int j = 0; j < 3; ++j) d[j] = r[j] - RI[j];
@@ -667,6 +682,17 @@ int orc_force(const orc_ctx* c, const double* V, const double* D, int n_sel, con
         free(part);
     }
     return err ? -1 : 0;
+}
+
+int orc_force(const orc_ctx* c, const double* V, const double* D, int n_sel, const int* atoms,
+              double* F, double* virial) {
+    return force_impl(c, V, D, n_sel, atoms, F, virial, NULL);
+}
+
+/* F_I and Pi_I from the grid points with mask[g] != 0 only (a shard of the grid). */
+int orc_force_masked(const orc_ctx* c, const double* V, const double* D, const unsigned char* mask, int n_sel,
+                     const int* atoms, double* F, double* virial) {
+    return force_impl(c, V, D, n_sel, atoms, F, virial, mask);
 }
 
 /* phi and grad phi of one species at displacements d (n x 3); for tests of

@@ -193,6 +193,9 @@ struct gint_handle {
     int n_ctas = 0;                   // persistent CTAs of the SIMT kernels
     int sm_count = 0;
     void* d_static = nullptr;         // device address of the library's static scratch array (not owned)
+    void* d_spec = nullptr;           // local potential: half spectrum of the grid (complex128)
+    double* d_epart = nullptr;        // local potential: per-block energy partial sums
+    int fft_fwd = -1, fft_inv = -1;   // local potential: cuFFT plans (made on first use)
     long long wait_limit = 0;         // polls of a bounded tensor-core pipeline wait (0: the default)
     int generation = 0;               // bumped by gint_update_positions (batches built earlier are stale)
     int brick_opt[3] = {0, 0, 0};     // brick shape asked for at set-up (0: default)

@@ -23,7 +23,7 @@ STATUS = {0: "GINT_OK", 1: "GINT_ERR_INVALID_ARG", 2: "GINT_ERR_CUDA", 3: "GINT_
 # exported symbols, in the order include/gint.h declares them
 SYMBOLS = ["gint_setup", "gint_destroy", "gint_pattern", "gint_set_precision", "gint_vlocal", "gint_rho",
            "gint_force_stress", "gint_energy_grads", "gint_update_positions", "gint_select_bricks", "gint_brick_loads",
-           "gint_set_wait_limit", "gint_debug_fail_alloc", "gint_vlocal_static", "gint_fold_k", "gint_check",
+           "gint_set_wait_limit", "gint_debug_fail_alloc", "gint_local_potential", "gint_vlocal_static", "gint_fold_k", "gint_check",
            "gint_batch_create", "gint_batch_run", "gint_batch_destroy", "gint_sync", "gint_get_info",
            "gint_work_stats", "gint_last_error"]
 
@@ -97,6 +97,8 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.gint_set_wait_limit.argtypes = [vp, i64]
     L.gint_debug_fail_alloc.restype = i32
     L.gint_debug_fail_alloc.argtypes = [i32]
+    L.gint_local_potential.restype = i32
+    L.gint_local_potential.argtypes = [vp] * 7
     L.gint_vlocal_static.restype = i32
     L.gint_vlocal_static.argtypes = [vp, vp, vp, vp]
     L.gint_fold_k.restype = i32
@@ -288,6 +290,21 @@ class Gint:
                                         _ptr(out.get("eps")), _ptr(out.get("V")), _ptr(out.get("D")),
                                         _ptr(out.get("E")), self._stream(stream)))
         return out
+
+    def local_potential(self, rho, V_ext=None, V_out=None, want_vh=False, stream=None):
+        """(V_out, V_H or None, energies (2,) = (E_H, E_xc)): V_out = V_ext + V_H + v_xc from rho."""
+        import torch
+        self._need(rho, self.n_grid, "rho")
+        if V_ext is not None:
+            self._need(V_ext, self.n_grid, "V_ext")
+        if V_out is None:
+            V_out = torch.empty(self.grid, dtype=torch.float64, device=rho.device)
+        self._need(V_out, self.n_grid, "V_out")
+        vh = torch.empty(self.grid, dtype=torch.float64, device=rho.device) if want_vh else None
+        en = torch.empty(2, dtype=torch.float64, device=rho.device)
+        _check(load().gint_local_potential(self._h, _ptr(rho), _ptr(V_ext), _ptr(V_out), _ptr(vh), _ptr(en),
+                                           self._stream(stream)))
+        return V_out, vh, en
 
     def supported(self) -> bool:
         """Whether the kernels of the current precision accept this handle's bricks."""
