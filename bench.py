@@ -214,6 +214,43 @@ def sample_errors(samples, H, rho, F, blocks, offsets):
     return {"H_abs": eh, "rho_rel": er, "F_abs": ef, "gates": {"H_abs": 1e-7, "rho_rel": 1e-6, "F_abs": 1e-5}}
 
 
+GOLDEN = os.path.join(ROOT, "tests", "golden", "tbg_oracle_samples.npz")
+
+
+def block_keys(blocks):
+    """One int64 per pattern block (I, J, t1, t2, t3), increasing with the pattern's sort order."""
+    import numpy as np
+    b = np.asarray(blocks, dtype=np.int64)
+    return ((((b[:, 0] << 14) + b[:, 1]) * 64 + b[:, 2] + 32) * 64 + b[:, 3] + 32) * 64 + b[:, 4] + 32
+
+
+def golden_errors(H, rho, F, blocks, offsets, path=GOLDEN):
+    """Errors against the cached FP64 oracle values of the TBG m=29 cell (written by
+    tests/golden/make_tbg_golden.py): H on its sampled blocks (max abs), rho at its points inside
+    the bilayer (normwise), F of its atoms (max abs)."""
+    import numpy as np
+    z = np.load(path)
+    keys = block_keys(z["h_keys"])
+    allk = block_keys(blocks)
+    pos = np.searchsorted(allk, keys)
+    if np.any(pos >= len(allk)) or np.any(allk[np.minimum(pos, len(allk) - 1)] != keys):
+        return {"error": "a cached block is missing from the pattern"}
+    Hn = H.cpu().numpy()
+    vals = z["h_vals"]
+    eh, o = 0.0, 0
+    for b in pos:
+        n = int(offsets[b + 1] - offsets[b])
+        eh = max(eh, float(np.max(np.abs(Hn[offsets[b]:offsets[b + 1]] - vals[o:o + n]))))
+        o += n
+    idx = z["r_idx"].astype(np.int64)
+    rg = rho[idx[:, 0], idx[:, 1], idx[:, 2]].cpu().numpy()
+    er = float(np.max(np.abs(rg - z["r_vals"])) / np.max(np.abs(z["r_vals"])))
+    ef = float(np.max(np.abs(F.cpu().numpy()[z["f_atoms"].astype(np.int64)] - z["f_vals"])))
+    return {"H_abs": eh, "rho_rel": er, "F_abs": ef, "gates": {"H_abs": 1e-7, "rho_rel": 1e-6, "F_abs": 1e-5},
+            "sample": f"cached oracle values: {len(keys)} blocks, {len(idx)} points inside the bilayer, "
+                      f"{len(z['f_atoms'])} atoms"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -493,6 +530,25 @@ def run_ours(args):
                "copies": "overlapped with the neighbouring steps" if args.e2e_overlap else "in line with the step"}
         del runner
 
+    # ---- the local potential from rho (Hartree by FFT + LDA XC), the step that feeds V back into
+    #      H^V; timed on its own, outside the metric's step
+    local_pot = None
+    if args.local_potential_steps > 0:
+        Vo = torch.empty_like(rho)
+        en = g.local_potential(rho, V_out=Vo)[2]
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(args.local_potential_steps):
+            g.local_potential(rho, V_out=Vo, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_lp = a.elapsed_time(b) / args.local_potential_steps
+        local_pot = {"ms_per_call": ms_lp, "grid_points_per_s": ng / (ms_lp / 1e3),
+                     "includes": "two 3-D FFTs (cuFFT, a library step), the G-space Hartree multiply and the "
+                                 "fused LDA pass with FP64 energies", "E_H": float(en[0]), "E_xc": float(en[1])}
+        del Vo
+
     # ---- roofline of the dominant call
     peaks, peak_src = load_peaks()
     sum_no, sum_no2 = g.work_stats()
@@ -547,6 +603,10 @@ def run_ours(args):
         if fp64 is not None:
             errors["fp64"] = sample_errors(samples, H_fp64, rho_fp64, F_fp64, blocks, offsets)
         errors["sample"] = "oracle outputs at the cpu_baseline sample (random points, blocks, atoms)"
+        if args.workload == "tbg_m29" and os.path.exists(GOLDEN):
+            errors["cached"] = {args.precision: golden_errors(H_mixed, rho_mixed, F_mixed, blocks, offsets)}
+            if fp64 is not None:
+                errors["cached"]["fp64"] = golden_errors(H_fp64, rho_fp64, F_fp64, blocks, offsets)
 
     gb = lambda n: f"{n * 8 / 1e9:.1f} GB"  # noqa: E731
     l2_note = (f"inputs larger than L2 (V {gb(ng)}, rho {gb(ng)}, D {gb(g.n_values)})" if ng * 8 > 256e6 else
@@ -563,6 +623,7 @@ def run_ours(args):
                        "parallelism": "replicas" if ws > 1 else "single", "setup_s": t_setup},
             "ms_per_call": {"vlocal": parts[0], "rho": parts[1], "force_stress": parts[2]},
             "fp64_form": fp64, "errors_vs_oracle": errors, "e2e": e2e, "roofline": roof, "cpu_baseline": cpu,
+            "local_potential": local_pot,
             "clocks": clocks.summary(), "gpu_launches": launches_per_step(forms) * args.steps}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -638,6 +699,7 @@ def main():
     ap.add_argument("--brick", type=int, nargs=3, default=[0, 0, 0])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--local-potential-steps", type=int, default=3)
     ap.add_argument("--e2e-overlap", action="store_true",
                     help="overlap each step's host copies with the neighbouring steps' compute (two copy streams)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -174,7 +174,8 @@ def test_batch_queue_vs_oracle(precision, cuda):
         eF = float(np.max(np.abs(F[i].cpu().numpy() - F_ref)))
         s_ref = -W_ref.sum(0) / o.omega
         eS = float(np.max(np.abs(sig[i].cpu().numpy() - s_ref)))
-        eE = abs(float(E[i]) - E_ref) / abs(E_ref)
+        # E = sum V rho dV cancels (V and rho change sign): relative to sum |V rho| dV
+        eE = abs(float(E[i]) - E_ref) / (float(np.sum(np.abs(V * r_ref))) * o.dV)
         print(f"{precision} cell {QUEUE_CELLS[i]} ({s.n_atoms} atoms, grid {s.grid[0]}^3, brick {bricks[i]}): "
               f"H {eH:.2e} (max {np.abs(H_ref).max():.2f}) rho {eR:.2e} F {eF:.2e} sigma {eS:.2e} E {eE:.2e}")
         assert eH < tol["H"] * max(1.0, float(np.max(np.abs(H_ref))))

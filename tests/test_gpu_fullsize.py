@@ -76,3 +76,58 @@ def test_fullsize_fp64_m29(cuda):
     eH, eR, eF, eE = run_case(29, "fp64", n_blocks=8, n_points=300, n_atoms=1)
     tol = TOL["fp64"]
     assert eH < tol["H"] and eR < tol["rho"] and eF < tol["F"] and eE < 1e-10
+
+
+# ---------------------------------------------------------- cached oracle values
+def _golden():
+    import os
+    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tbg_oracle_samples.npz")
+    if not os.path.exists(p):
+        pytest.fail("tests/golden/tbg_oracle_samples.npz is missing (tests/golden/make_tbg_golden.py writes it)")
+    return p, np.load(p)
+
+
+def test_fullsize_m29_against_cached_oracle(cuda):
+    """TBG m=29 in the benchmark's forms (H^V and rho exact, force three-product), 8x8x8 bricks,
+    against cached FP64 oracle values: 1,000 blocks of H, 10,000 points of rho inside the
+    bilayer and the forces of 8 atoms, element by element."""
+    import bench
+    from paper_2409_09399_gb300 import gint
+    path, z = _golden()
+    s = synth.tbg(29)
+    g = gint.from_system(s, precision="fp16x4", brick=(8, 8, 8))
+    V = synth.v_grid(s.grid, synth.plane_wave_params(), device="cuda")
+    blocks, offsets = g.pattern()
+    D = synth.d_fill_torch(blocks, offsets[:-1], g.n_values, s.pos, s.cell, s.nw(), "cuda")
+    H = g.vlocal(V)
+    rho = g.rho(D)
+    g.set_precision("fp16x3")
+    F, _, _, _ = g.force_stress(V, D)
+    g.sync()
+    assert len(z["h_keys"]) >= 1000 and len(z["r_idx"]) >= 10000 and len(z["f_atoms"]) >= 8
+    e = bench.golden_errors(H, rho, F, blocks, offsets, path)
+    print(f"TBG m=29 vs cached oracle ({e['sample']}): H {e['H_abs']:.2e} rho {e['rho_rel']:.2e} F {e['F_abs']:.2e}")
+    assert e["H_abs"] < 1e-7 and e["rho_rel"] < 1e-6 and e["F_abs"] < 1e-5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp16x4", "fp16x3"])
+def test_stress_m5_against_cached_oracle(precision, cuda):
+    """TBG m=5: every force and the stress (from the full per-atom virial) against the cached
+    oracle values (Eq. 4, 5)."""
+    from paper_2409_09399_gb300 import gint
+    _, z = _golden()
+    s = synth.tbg(int(z["m5"]))
+    g = gint.from_system(s, precision=precision, brick=(8, 8, 8))
+    V = synth.v_grid(s.grid, synth.plane_wave_params(), device="cuda")
+    blocks, offsets = g.pattern()
+    D = synth.d_fill_torch(blocks, offsets[:-1], g.n_values, s.pos, s.cell, s.nw(), "cuda")
+    F, sigma, vir, E = g.force_stress(V, D)
+    g.sync()
+    eF = float(np.max(np.abs(F.cpu().numpy() - z["m5_F"])))
+    eV = float(np.max(np.abs(vir.cpu().numpy() - z["m5_vir"])))
+    eS = float(np.max(np.abs(sigma.cpu().numpy() - z["m5_sigma"])))
+    smax = float(np.max(np.abs(z["m5_sigma"])))
+    print(f"TBG m={int(z['m5'])} {precision}: F {eF:.2e} per-atom virial {eV:.2e} sigma {eS:.2e} (max |sigma| {smax:.2e})")
+    tolF = {"fp64": 1e-10, "fp16x4": 1e-5, "fp16x3": 1e-5}[precision]
+    tolS = {"fp64": 1e-12, "fp16x4": 1e-6, "fp16x3": 1e-4}[precision]  # as on the diamond cell
+    assert eF < tolF and eS < tolS
