@@ -166,6 +166,19 @@ def oracle_sample(system, n_points, n_blocks, n_atoms_f, seed=11, inputs=None):
     return full, desc, samples
 
 
+def oracle_sample_parts(system, n_points, n_blocks, inputs, seed=17):
+    """Seconds the oracle takes for n_points rho points and n_blocks H blocks (a fixed sample)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    o, V, D = inputs
+    idx = np.stack([rng.integers(0, system.grid[i], n_points) for i in range(3)], 1)
+    keys = o.blocks[rng.choice(len(o.blocks), size=min(n_blocks, len(o.blocks)), replace=False)]
+    t0 = time.perf_counter()
+    o.rho_points(D, idx)
+    o.vlocal_blocks(V, keys)
+    return time.perf_counter() - t0, f"{n_points} rho points and {len(keys)} H blocks"
+
+
 CALLS = ("vlocal", "rho", "force")
 TC_PRODUCTS = {"fp16x3": 3, "bf16x3": 3, "fp16x4": 6}  # 16-bit tensor products per credited product
 DTYPES = {"fp64": "f64", "fp32": "f32", "fp16x3": "f16x3", "bf16x3": "bf16x3", "fp16x4": "f16x4"}
@@ -596,9 +609,25 @@ def run_ours(args):
     errors = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
-        t_full, sample, samples = oracle_sample(system, args.ref_points, args.ref_blocks, args.ref_atoms)
-        cpu = {"value": ng / t_full, "unit": "grid_points/s", "cores": oracle.num_threads(), "kind": "oracle",
+        inputs = oracle_inputs(system)
+        t_full, sample, samples = oracle_sample(system, args.ref_points, args.ref_blocks, args.ref_atoms,
+                                                inputs=inputs)
+        cores = oracle.num_threads()
+        cpu = {"value": ng / t_full, "unit": "grid_points/s", "cores": cores, "kind": "oracle",
                "sample": json.dumps(sample)}
+        # one thread: a smaller sample of rho points and H blocks; the force part is scaled from the
+        # all-core force time by the one-thread / all-core ratio of the other two parts
+        if args.ref_points_1thread > 0:
+            oracle.set_num_threads(1)
+            try:
+                t1, s1 = oracle_sample_parts(system, args.ref_points_1thread, args.ref_blocks_1thread, inputs)
+            finally:
+                oracle.set_num_threads(cores)
+            tN, _ = oracle_sample_parts(system, args.ref_points_1thread, args.ref_blocks_1thread, inputs)
+            ratio = t1 / tN
+            cpu["one_thread"] = {"value": ng / (t_full * ratio), "unit": "grid_points/s", "cores": 1,
+                                 "sample": f"{s1}; one-thread / {cores}-thread time ratio {ratio:.2f} on that "
+                                           "sample, applied to the whole all-core step estimate"}
         errors = {args.precision: sample_errors(samples, H_mixed, rho_mixed, F_mixed, blocks, offsets)}
         if fp64 is not None:
             errors["fp64"] = sample_errors(samples, H_fp64, rho_fp64, F_fp64, blocks, offsets)
@@ -698,14 +727,17 @@ def main():
                     help=f"one form for every call, or one per call (default {DEFAULT_FORMS}; batches: fp16x4)")
     ap.add_argument("--brick", type=int, nargs=3, default=[0, 0, 0])
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--local-potential-steps", type=int, default=3)
-    ap.add_argument("--e2e-overlap", action="store_true",
-                    help="overlap each step's host copies with the neighbouring steps' compute (two copy streams)")
+    ap.add_argument("--e2e-inline", dest="e2e_overlap", action="store_false",
+                    help="keep each step's host copies in line with its compute (default: overlap them with the "
+                         "neighbouring steps' compute on two copy streams)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-points", type=int, default=2000)
     ap.add_argument("--ref-blocks", type=int, default=24)
     ap.add_argument("--ref-atoms", type=int, default=1)
+    ap.add_argument("--ref-points-1thread", type=int, default=400)
+    ap.add_argument("--ref-blocks-1thread", type=int, default=6)
     args = ap.parse_args()
     if args.precision is None:
         args.precision = "fp16x4" if args.workload.startswith("batch") else DEFAULT_FORMS

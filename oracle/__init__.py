@@ -71,12 +71,18 @@ def lib():
         L.orc_force_masked.argtypes = [vp, _f64p, _f64p, _u8p, ctypes.c_int, _i32p, _f64p, _f64p]
         L.orc_eval_orbitals.argtypes = [vp, ctypes.c_int, ctypes.c_int64, _f64p, _f64p, _f64p]
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib = L
     return _lib
 
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int):
+    """OpenMP threads of later oracle calls (n >= 1)."""
+    lib().orc_set_num_threads(int(n))
 
 
 class Oracle:

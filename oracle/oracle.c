@@ -711,6 +711,14 @@ void orc_eval_orbitals(const orc_ctx* c, int species, int64_t n, const double* d
     }
 }
 
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

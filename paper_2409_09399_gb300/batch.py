@@ -21,11 +21,14 @@ CANDIDATE_BRICKS: Tuple[Tuple[int, int, int], ...] = ((8, 8, 8), (4, 8, 8), (4, 
                                                       (2, 2, 2))
 
 
-def _inputs(system, g):
-    import synth
-    V = synth.v_grid(system.grid, synth.plane_wave_params(), device="cuda")
-    blocks, offsets = g.pattern()
-    D = synth.d_fill_torch(blocks, offsets[:-1], g.n_values, system.pos, system.cell, system.nw(), "cuda")
+def _timing_inputs(g, seed=0):
+    """V and D for timing only: seeded uniform values of the right sizes (the kernels' work does not
+    depend on the values), so the autotuner needs nothing from the caller's inputs."""
+    import torch
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    V = torch.rand(g.grid, dtype=torch.float64, device="cuda", generator=gen) - 0.5
+    D = torch.rand(g.n_values, dtype=torch.float64, device="cuda", generator=gen) - 0.5
     return V, D
 
 
@@ -51,7 +54,6 @@ def autotune_brick(systems: Sequence, precision="fp16x3", candidates=CANDIDATE_B
     rng = np.random.default_rng(seed)
     idx = [int(i) for i in rng.choice(len(systems), size=min(sample, len(systems)), replace=False)]
     table: Dict[tuple, Dict[int, Optional[float]]] = {}
-    inputs = {}
     for brick in candidates:
         brick = tuple(brick)
         table[brick] = {}
@@ -65,7 +67,7 @@ def autotune_brick(systems: Sequence, precision="fp16x3", candidates=CANDIDATE_B
                 if not g.supported():
                     table[brick][i] = None
                     continue
-                V, D = _inputs(systems[i], g)
+                V, D = _timing_inputs(g)
                 table[brick][i] = _time_calls(g, V, D)
             finally:
                 g.close()
