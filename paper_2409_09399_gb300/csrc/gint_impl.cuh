@@ -188,8 +188,6 @@ struct gint_handle {
     void* d_dt = nullptr;             // per-call 16x16 tensor-core copy of D (1 KB per block)
     int* d_dq = nullptr;              // exact form: per (atom, orbital row) max |D| bits, n_atoms x 16
     void* d_zero = nullptr;           // one zero tile of the tensor-core copy of D
-    float* d_psi = nullptr;           // tensor-core H^V: per-CTA store of a brick's orbital values
-    float* d_psi_rf = nullptr;        // tensor-core rho/force: per-CTA store of a tile's orbital values
     void* d_scratch = nullptr;
     size_t scratch_bytes = 0;
     int n_ctas = 0;                   // persistent CTAs of the SIMT kernels

@@ -949,7 +949,7 @@ static void free_handle(gint_handle* h) {
     void* ptrs[] = {h->d_sp, h->d_coef64, h->d_coef32, h->d_knot32, h->d_ext, h->d_blocks, h->d_offsets, h->d_row_start,
                     h->d_mirror, h->d_brick_start, h->d_brick_atoms, h->d_work, h->d_pair_start, h->d_pairs, h->d_tile_mask, h->d_empty, h->d_err, h->d_red,
                     h->d_scratch, h->d_nw_atom, h->d_atom_sp, h->d_orb_off, h->d_facc, h->d_dt, h->d_dq, h->d_zero,
-                    h->d_spec, h->d_epart, h->d_psi, h->d_psi_rf};
+                    h->d_spec, h->d_epart};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (prev >= 0) cudaSetDevice(prev);

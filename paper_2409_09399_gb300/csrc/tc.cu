@@ -69,11 +69,6 @@ template <bool kExact> struct TcCfg {
     static constexpr int kPassCols = kExact ? 256 : 512;      // output columns per pass
 };
 
-// Per-CTA region of the orbital-value store (TcArgs::psi): rows x points for the largest brick of
-// either form.
-constexpr int kPsiRows = TcCfg<true>::kRows > TcCfg<false>::kRows ? TcCfg<true>::kRows : TcCfg<false>::kRows;
-constexpr int kPsiPts = TcCfg<true>::kPts > TcCfg<false>::kPts ? TcCfg<true>::kPts : TcCfg<false>::kPts;
-
 struct TcAtom {
     float c_hi[3], c_lo[3];  // (brick origin - atom image position), FP64 split into two FP32 words
     int I;
@@ -87,7 +82,6 @@ struct TcArgs {
     Problem P;
     int* counter;
     long wait_limit;  // polls of a bounded hand-off wait (producers <-> MMA issue)
-    float* psi;       // per-CTA store of a brick's orbital values (kRows x kPts FP32 per CTA), or null
     int norm_after;  // exact form: leave the harmonic normalisation to k_norm_h (H not accumulated into)
 };
 
@@ -397,11 +391,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
         __syncthreads();
 
         const int nchunks = g.bpad / kTcChunk;
-        // A brick with more than one pass evaluates its orbital values once: pass 0 evaluates every
-        // atom image at every point and keeps the values (as split, FP32) in this CTA's region of
-        // A.psi (L2-resident); later passes read them back instead of evaluating them again.
-        const bool reuse = A.psi != nullptr && npass > 1;
-        float* const psi = reuse ? A.psi + (size_t)blockIdx.x * kPsiRows * kPsiPts : nullptr;
         for (int pass = 0; pass < npass && !S.abort; ++pass) {
             const int s0p = S.pass_first[pass], s1p = S.pass_first[pass + 1];
             const int t_lo = 128 * S.seg_tile[s0p], t_hi = 128 * (S.seg_tile[s1p - 1] + 1);
@@ -419,7 +408,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                         const int r0 = S.at[a].off, r1 = r0 + S.at[a].nw;
                         nd = r0 < t_hi && r1 > t_lo;
                         for (int sg = s0p; sg < s1p; ++sg) nd = nd || (r0 < S.seg_c1[sg] && r1 > S.seg_c0[sg]);
-                        if (reuse && pass == 0) nd = true;  // pass 0 keeps every image's values
                     }
                     m |= (uint64_t)__ballot_sync(0xffffffffu, nd) << (32 * h2);
                 }
@@ -474,14 +462,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                         const int qoff = ((q >> 3) << 7) + ((q & 7) << 1);
                         const int rbase = X.off;
                         const SpeciesFast& sf = S.spf[X.sp];
-                        // the 16-bit pieces of A = 2^s W psi and B = psi for row r at this point pair
-                        // (va, vb: the values as split; exact form: unnormalised and scaled by the
-                        // row's quantum)
-                        auto emit = [&](int o, float va, float vb) {
+                        auto put2 = [&](int o, float va, float vb) {
                             const int r = rbase + o;
                             const int offB = kBOff + S.rowtab[r] + qoff;
                             auto st32 = [&](int off, uint32_t x) { *reinterpret_cast<uint32_t*>(&buf[off]) = x; };
                             if (kExact) {
+                                const float qi = exp2i(-sf.qeu[o]);  // unnormalised orbital values
+                                va *= qi;
+                                vb *= qi;
                                 uint32_t n, p, q;
                                 if (r >= a_lo && r < a_hi) {
                                     const int offA = S.rowtab[r - a_lo] + qoff;
@@ -499,40 +487,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                                 st32(offB, bh); st32(offB + kBP, bl);
                             }
                         };
-                        if (reuse && pass > 0) {
-                            // values kept by pass 0 of this brick (rows x points, two points per load)
-                            const float* src = psi + (size_t)rbase * kPsiPts + p;
+                        if (!orbitals_fast2<!kExact>(sf, knot2, ax, ay, az, bx, by, bz, put2))
                             for (int o = 0; o < X.nw; ++o) {
-                                const float2 v = __ldcg(reinterpret_cast<const float2*>(src + (size_t)o * kPsiPts));
-                                emit(o, v.x, v.y);
+                                const int r = rbase + o;
+                                const int offB = kBOff + S.rowtab[r] + qoff;
+                                const bool inA = r >= a_lo && r < a_hi;
+                                const int offA = inA ? S.rowtab[r - a_lo] + qoff : 0;
+                                for (int pc = 0; pc < C::kPieces; ++pc) {
+                                    *reinterpret_cast<uint32_t*>(&buf[offB + pc * kBP]) = 0u;
+                                    if (inA) *reinterpret_cast<uint32_t*>(&buf[offA + pc * kAP]) = 0u;
+                                }
                             }
-                        } else {
-                            auto put2 = [&](int o, float va, float vb) {
-                                if (kExact) {
-                                    const float qi = exp2i(-sf.qeu[o]);  // unnormalised orbital values
-                                    va *= qi;
-                                    vb *= qi;
-                                }
-                                if (reuse)
-                                    __stcg(reinterpret_cast<float2*>(psi + (size_t)(rbase + o) * kPsiPts + p),
-                                           make_float2(va, vb));
-                                emit(o, va, vb);
-                            };
-                            if (!orbitals_fast2<!kExact>(sf, knot2, ax, ay, az, bx, by, bz, put2))
-                                for (int o = 0; o < X.nw; ++o) {
-                                    const int r = rbase + o;
-                                    const int offB = kBOff + S.rowtab[r] + qoff;
-                                    const bool inA = r >= a_lo && r < a_hi;
-                                    const int offA = inA ? S.rowtab[r - a_lo] + qoff : 0;
-                                    for (int pc = 0; pc < C::kPieces; ++pc) {
-                                        *reinterpret_cast<uint32_t*>(&buf[offB + pc * kBP]) = 0u;
-                                        if (inA) *reinterpret_cast<uint32_t*>(&buf[offA + pc * kAP]) = 0u;
-                                    }
-                                    if (reuse)
-                                        __stcg(reinterpret_cast<float2*>(psi + (size_t)r * kPsiPts + p),
-                                               make_float2(0.f, 0.f));
-                                }
-                        }
                     }
                     tc::fence_async_smem();
                     tc::mbar_arrive(&S.full[b]);
@@ -719,10 +684,6 @@ gint_status tc_vlocal(gint_handle* h, int form, const double* V, double* H, int 
     A.P = h->problem();
     A.counter = h->d_err + 2;
     A.wait_limit = wait_polls(h);
-    if (!h->d_psi) {  // one region per persistent CTA, sized for the largest brick of either form
-        GINT_CUDA_TRY(dev_malloc(&h->d_psi, sizeof(float) * (size_t)kPsiRows * kPsiPts * (size_t)std::max(1, h->sm_count)));
-    }
-    A.psi = h->d_psi;
     GINT_CUDA_TRY(cudaMemsetAsync(A.counter, 0, sizeof(int), st));
     const size_t smem = exact ? tc_smem_bytes<true>() : tc_smem_bytes<false>();
 #define GINT_LAUNCH_VL(H16, X)                                                                                 \

@@ -229,7 +229,7 @@ __global__ void k_format_d(Problem P, const int32_t* mirror, const int* nw_atom,
 // problem and the buffers of an item come from its cell's CellJob.
 template <typename H16, bool kForce, bool kExact, bool kMulti>
 __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_constant__ CellJob J_in, int* counter, const __grid_constant__ MultiArgs M,
-                                                                 long wait_limit, float* psi_all) {
+                                                                 long wait_limit) {
     constexpr int kCols = kExact ? kMaxCols / 2 : kMaxCols;  // output columns of one column group
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Smem<kExact>& S = *reinterpret_cast<Smem<kExact>*>(smem_raw);
@@ -378,12 +378,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
             // piece, is exactly the slot's 16-byte rows in the K-major B layout; the copies
             // of step s + 1 start as soon as the MMAs of step s - 1 complete.
             const int nsteps = (nact + 1) >> 1;
-            // A tile with more than one column group runs the K loop once per group over the same
-            // K images: the first group evaluates the orbital values and keeps them (FP32,
-            // [image][orbital][point], this CTA's L2-resident region of psi_all); later groups read
-            // them back instead of evaluating them again.
-            const bool keep = psi_all != nullptr && nact > kCols / 16;
-            float* const psi = keep ? psi_all + (size_t)blockIdx.x * kMaxAtoms * 16 * 128 : nullptr;
             if (warp < kProdWarps) {
                 const int j = tid >> 7, pl = tid & 127;
                 for (int st = 0; st < nsteps; ++st) {
@@ -394,41 +388,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
                         const Atom& X = S.at[S.act[k + j]];
                         const int p = mt * 128 + pl;
                         unsigned char* A0 = S.A[b][j];
-                        float* const pk = keep ? psi + (size_t)(k + j) * 16 * 128 + pl : nullptr;  // + o * 128
                         for (int o = X.nw; o < 16; ++o)
                             for (int pc = 0; pc < C::kPieces; ++pc)
                                 *reinterpret_cast<unsigned short*>(A0 + pc * kAPiece + amn(pl, o)) = 0;
-                        auto put = [&](int o, float v, float, float, float) {
-                            unsigned short hi, lo, l2 = 0;
-                            if (kExact) fix_split3(v * qa_inv, hi, lo, l2);
-                            else Split<H16>::run(v, hi, lo);
-                            *reinterpret_cast<unsigned short*>(A0 + amn(pl, o)) = hi;
-                            *reinterpret_cast<unsigned short*>(A0 + kAPiece + amn(pl, o)) = lo;
-                            if (kExact) *reinterpret_cast<unsigned short*>(A0 + 2 * kAPiece + amn(pl, o)) = l2;
-                        };
-                        if (keep && cg0 > 0) {
-                            for (int o = 0; o < X.nw; ++o) put(o, __ldcg(pk + o * 128), 0.f, 0.f, 0.f);
-                        } else {
-                            bool inside = false;
-                            if (p < g.bpts) {
-                                float fx, fy, fz;
-                                point_offset(g, p, fx, fy, fz);
-                                const float dx = (X.c_hi[0] + fx) + X.c_lo[0];
-                                const float dy = (X.c_hi[1] + fy) + X.c_lo[1];
-                                const float dz = (X.c_hi[2] + fz) + X.c_lo[2];
-                                auto put_keep = [&](int o, float v, float gx, float gy, float gz) {
-                                    if (keep) __stcg(pk + o * 128, v);
-                                    put(o, v, gx, gy, gz);
-                                };
-                                inside = orbitals_fast<false>(S.spf[X.sp], knot2, dx, dy, dz, put_keep);
-                            }
-                            if (!inside)
-                                for (int o = 0; o < X.nw; ++o) {
-                                    for (int pc = 0; pc < C::kPieces; ++pc)
-                                        *reinterpret_cast<unsigned short*>(A0 + pc * kAPiece + amn(pl, o)) = 0;
-                                    if (keep) __stcg(pk + o * 128, 0.f);
-                                }
+                        bool inside = false;
+                        if (p < g.bpts) {
+                            float fx, fy, fz;
+                            point_offset(g, p, fx, fy, fz);
+                            const float dx = (X.c_hi[0] + fx) + X.c_lo[0];
+                            const float dy = (X.c_hi[1] + fy) + X.c_lo[1];
+                            const float dz = (X.c_hi[2] + fz) + X.c_lo[2];
+                            auto put = [&](int o, float v, float, float, float) {
+                                unsigned short hi, lo, l2 = 0;
+                                if (kExact) fix_split3(v * qa_inv, hi, lo, l2);
+                                else Split<H16>::run(v, hi, lo);
+                                *reinterpret_cast<unsigned short*>(A0 + amn(pl, o)) = hi;
+                                *reinterpret_cast<unsigned short*>(A0 + kAPiece + amn(pl, o)) = lo;
+                                if (kExact) *reinterpret_cast<unsigned short*>(A0 + 2 * kAPiece + amn(pl, o)) = l2;
+                            };
+                            inside = orbitals_fast<false>(S.spf[X.sp], knot2, dx, dy, dz, put);
                         }
+                        if (!inside)
+                            for (int o = 0; o < X.nw; ++o)
+                                for (int pc = 0; pc < C::kPieces; ++pc)
+                                    *reinterpret_cast<unsigned short*>(A0 + pc * kAPiece + amn(pl, o)) = 0;
                     }
                     tc::fence_async_smem();
                     tc::mbar_arrive(&S.full[b]);
@@ -695,7 +678,7 @@ CellJob tc_cell_job(gint_handle* h, const double* V, double* H, double* rho, dou
 
 // One launch of the rho or force kernel: one cell (M.n_items == 0: J) or a batch queue (M).
 static gint_status launch_rf(int form, bool force, const CellJob& J, const MultiArgs& M, bool multi, int* counter,
-                             int sm_count, long wait_limit, float* psi, cudaStream_t st) {
+                             int sm_count, long wait_limit, cudaStream_t st) {
     const bool exact = form == 2;
     GINT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
     const size_t smem = (exact ? sizeof(Smem<true>) : sizeof(Smem<false>)) + 1024;
@@ -703,7 +686,7 @@ static gint_status launch_rf(int form, bool force, const CellJob& J, const Multi
     do {                                                                                                        \
         GINT_CUDA_TRY(cudaFuncSetAttribute(k_rhoforce_tc<H16, F, X, MU>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                            (int)smem));                                                         \
-        k_rhoforce_tc<H16, F, X, MU><<<sm_count, kThreads, smem, st>>>(J, counter, M, wait_limit, psi);          \
+        k_rhoforce_tc<H16, F, X, MU><<<sm_count, kThreads, smem, st>>>(J, counter, M, wait_limit);               \
     } while (0)
 #define GINT_LAUNCH_RF2(H16, X, MU) \
     do { if (force) GINT_LAUNCH_RF(H16, true, X, MU); else GINT_LAUNCH_RF(H16, false, X, MU); } while (0)
@@ -728,11 +711,8 @@ gint_status tc_rhoforce(gint_handle* h, int form, bool force, const double* V, c
     if (s != GINT_OK) return s;
     s = tc_format_d(h, form, D, st);
     if (s != GINT_OK || h->n_work == 0) return s;
-    if (!h->d_psi_rf)  // one region per persistent CTA: every image's orbital values at a 128-point tile
-        GINT_CUDA_TRY(dev_malloc(&h->d_psi_rf, sizeof(float) * (size_t)kMaxAtoms * 16 * 128 *
-                                                   (size_t)std::max(1, h->sm_count)));
     return launch_rf(form, force, tc_cell_job(h, V, nullptr, rho, facc, acc_e), MultiArgs{}, false, h->d_err + 2,
-                     h->sm_count, wait_polls(h), h->d_psi_rf, st);
+                     h->sm_count, wait_polls(h), st);
 }
 
 // One launch over the (cell, brick) queue of a batch (every cell's D formatted, cells checked).
@@ -740,7 +720,7 @@ gint_status tc_rhoforce_multi(int form, bool force, const MultiArgs& M, int* cou
     if (M.n_items == 0) return GINT_OK;
     CellJob none;
     memset(&none, 0, sizeof(none));
-    return launch_rf(form, force, none, M, true, counter, sm_count, kDefaultWaitPolls, nullptr, st);
+    return launch_rf(form, force, none, M, true, counter, sm_count, kDefaultWaitPolls, st);
 }
 
 }  // namespace gint
