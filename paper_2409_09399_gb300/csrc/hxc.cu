@@ -85,31 +85,48 @@ struct Recip {
 // the Nyquist index of an even axis stands for both +n/2 and -n/2; the kernel there is the
 // mean of the two assignments related by G -> -G, which keeps V_H(G) Hermitian (so the
 // real inverse transform is exact) and equals the real part of the full complex transform
-// with the -n/2 assignment.
-__global__ void k_hartree_g(double2* spec, int n0, int n1, int n2, Recip R, double inv_n) {
+// with the -n/2 assignment.  One CTA per (i0, i1) row of the spectrum, threads along i2
+// (contiguous), 32-bit index arithmetic; the only FP64 division is 1/|G|^2 (two on the
+// Nyquist planes).
+__global__ void k_hartree_g(double2* spec, int n0, int n1, int n2, Recip R, double c4pi_n) {
     const int h2 = n2 / 2 + 1;
-    const int64_t total = (int64_t)n0 * n1 * h2;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int i2 = (int)(e % h2);
-        const int64_t r = e / h2;
-        const int i1 = (int)(r % n1), i0 = (int)(r / n1);
-        const int m0 = freq(i0, n0), m1 = freq(i1, n1), m2 = freq(i2, n2);
-        // -G with each Nyquist component kept at -n/2
-        const int q0 = (2 * i0 == n0) ? m0 : -m0;
+    for (int row = blockIdx.x; row < n0 * n1; row += gridDim.x) {
+        const int i0 = row / n1, i1 = row - i0 * n1;
+        const int m0 = freq(i0, n0), m1 = freq(i1, n1);
+        const int q0 = (2 * i0 == n0) ? m0 : -m0;  // -G with each Nyquist component kept at -n/2
         const int q1 = (2 * i1 == n1) ? m1 : -m1;
-        const int q2 = (2 * i2 == n2) ? m2 : -m2;
-        const double k = 0.5 * (coulomb(R.b, m0, m1, m2) + coulomb(R.b, q0, q1, q2)) * inv_n;
-        double2 v = spec[e];
-        v.x *= k;
-        v.y *= k;
-        spec[e] = v;
+        const bool nyq01 = (q0 == m0 && m0 != 0) || (q1 == m1 && m1 != 0);
+        // in-plane part of G and of its partner
+        const double gx = m0 * R.b[0] + m1 * R.b[3], gy = m0 * R.b[1] + m1 * R.b[4], gz = m0 * R.b[2] + m1 * R.b[5];
+        const double qx = q0 * R.b[0] + q1 * R.b[3], qy = q0 * R.b[1] + q1 * R.b[4], qz = q0 * R.b[2] + q1 * R.b[5];
+        double2* line = spec + (size_t)row * h2;
+        for (int i2 = threadIdx.x; i2 < h2; i2 += blockDim.x) {
+            const int m2 = freq(i2, n2);
+            const double ax = fma((double)m2, R.b[6], gx), ay = fma((double)m2, R.b[7], gy);
+            const double az = fma((double)m2, R.b[8], gz);
+            const double g2 = fma(ax, ax, fma(ay, ay, az * az));
+            double k = g2 > 0.0 ? c4pi_n / g2 : 0.0;
+            const bool nyq2 = 2 * i2 == n2;
+            if (nyq01 || nyq2) {  // Nyquist planes: mean with the partner assignment
+                const int q2 = nyq2 ? m2 : -m2;
+                const double bx = fma((double)q2, R.b[6], qx), by = fma((double)q2, R.b[7], qy);
+                const double bz = fma((double)q2, R.b[8], qz);
+                const double p2 = fma(bx, bx, fma(by, by, bz * bz));
+                k = 0.5 * (k + (p2 > 0.0 ? c4pi_n / p2 : 0.0));
+            }
+            double2 v = line[i2];
+            v.x *= k;
+            v.y *= k;
+            line[i2] = v;
+        }
     }
 }
 
 // LDA exchange-correlation per electron and potential at density rho > 0 (hartree).
 __device__ __forceinline__ void lda_xc(double rho, double& eps, double& v) {
     const double rs = cbrt(3.0 / (4.0 * M_PI * rho));
-    const double ex = -0.75 * cbrt(9.0 / (4.0 * M_PI * M_PI)) / rs;  // Slater exchange
+    constexpr double kSlater = -0.75 * 0.6108870577108572;  // -(3/4) (9 / (4 pi^2))^(1/3)
+    const double ex = kSlater / rs;  // Slater exchange
     const double vx = (4.0 / 3.0) * ex;
     double ec, vc;
     if (rs >= 1.0) {  // Perdew-Zunger 1981, rs >= 1
@@ -277,8 +294,8 @@ extern "C" gint_status gint_local_potential(gint_handle* h, const double* rho, c
         for (int j = 0; j < 3; ++j)
             for (int c = 0; c < 3; ++c) R.b[3 * j + c] = 2.0 * M_PI * inv[3 * c + j];
     }
-    const int blocks = 8 * std::max(1, h->sm_count);
-    k_hartree_g<<<blocks, 256, 0, st>>>(spec, (int)n0, (int)n1, (int)n2, R, 1.0 / (double)(n0 * n1 * n2));
+    const int blocks = (int)std::min<int64_t>(n0 * n1, (int64_t)64 * std::max(1, h->sm_count));
+    k_hartree_g<<<blocks, 128, 0, st>>>(spec, (int)n0, (int)n1, (int)n2, R, 4.0 * M_PI / (double)(n0 * n1 * n2));
     GINT_CUDA_TRY(cudaGetLastError());
     GINT_FFT_TRY(g_fft.exec_z2d((cufftHandle)h->fft_inv, (cufftDoubleComplex*)spec, vh));
     k_local_potential<<<kRedBlocks, kRedThreads, 0, st>>>(rho, V_ext, vh, V_out, n0 * n1 * n2, h->d_epart);
