@@ -68,6 +68,13 @@ constexpr int kRedThreads = 256;
 // (the Nyquist index of an even axis is -n/2).
 __device__ __forceinline__ int freq(int i, int n) { return i < (n + 1) / 2 ? i : i - n; }
 
+// 1/x for x > 0 in FP64 from the FP32 reciprocal and one Newton-Raphson step
+// y <- y (2 - x y), which squares the relative error (2^-23 -> below 2^-45).
+__device__ __forceinline__ double recip(double x) {
+    const double y = (double)__frcp_rn((float)x);
+    return y * fma(-x, y, 2.0);
+}
+
 // 4 pi / |G|^2 for G = m0 b0 + m1 b1 + m2 b2 (b: reciprocal rows, b_i . a_j = 2 pi delta_ij).
 __device__ __forceinline__ double coulomb(const double b[9], int m0, int m1, int m2) {
     const double gx = m0 * b[0] + m1 * b[3] + m2 * b[6];
@@ -86,8 +93,8 @@ struct Recip {
 // mean of the two assignments related by G -> -G, which keeps V_H(G) Hermitian (so the
 // real inverse transform is exact) and equals the real part of the full complex transform
 // with the -n/2 assignment.  One CTA per (i0, i1) row of the spectrum, threads along i2
-// (contiguous), 32-bit index arithmetic; the only FP64 division is 1/|G|^2 (two on the
-// Nyquist planes).
+// (contiguous), 32-bit index arithmetic; 1/|G|^2 from the FP32 reciprocal refined once in
+// FP64 (two on the Nyquist planes).
 __global__ void k_hartree_g(double2* spec, int n0, int n1, int n2, Recip R, double c4pi_n) {
     const int h2 = n2 / 2 + 1;
     for (int row = blockIdx.x; row < n0 * n1; row += gridDim.x) {
@@ -105,14 +112,14 @@ __global__ void k_hartree_g(double2* spec, int n0, int n1, int n2, Recip R, doub
             const double ax = fma((double)m2, R.b[6], gx), ay = fma((double)m2, R.b[7], gy);
             const double az = fma((double)m2, R.b[8], gz);
             const double g2 = fma(ax, ax, fma(ay, ay, az * az));
-            double k = g2 > 0.0 ? c4pi_n / g2 : 0.0;
+            double k = g2 > 0.0 ? c4pi_n * recip(g2) : 0.0;
             const bool nyq2 = 2 * i2 == n2;
             if (nyq01 || nyq2) {  // Nyquist planes: mean with the partner assignment
                 const int q2 = nyq2 ? m2 : -m2;
                 const double bx = fma((double)q2, R.b[6], qx), by = fma((double)q2, R.b[7], qy);
                 const double bz = fma((double)q2, R.b[8], qz);
                 const double p2 = fma(bx, bx, fma(by, by, bz * bz));
-                k = 0.5 * (k + (p2 > 0.0 ? c4pi_n / p2 : 0.0));
+                k = 0.5 * (k + (p2 > 0.0 ? c4pi_n * recip(p2) : 0.0));
             }
             double2 v = line[i2];
             v.x *= k;
@@ -295,7 +302,9 @@ extern "C" gint_status gint_local_potential(gint_handle* h, const double* rho, c
             for (int c = 0; c < 3; ++c) R.b[3 * j + c] = 2.0 * M_PI * inv[3 * c + j];
     }
     const int blocks = (int)std::min<int64_t>(n0 * n1, (int64_t)64 * std::max(1, h->sm_count));
-    k_hartree_g<<<blocks, 128, 0, st>>>(spec, (int)n0, (int)n1, (int)n2, R, 4.0 * M_PI / (double)(n0 * n1 * n2));
+    const int h2 = (int)(n2 / 2 + 1);
+    const int threads = std::min(256, (h2 + 31) / 32 * 32);  // one pass over a spectrum row
+    k_hartree_g<<<blocks, threads, 0, st>>>(spec, (int)n0, (int)n1, (int)n2, R, 4.0 * M_PI / (double)(n0 * n1 * n2));
     GINT_CUDA_TRY(cudaGetLastError());
     GINT_FFT_TRY(g_fft.exec_z2d((cufftHandle)h->fft_inv, (cufftDoubleComplex*)spec, vh));
     k_local_potential<<<kRedBlocks, kRedThreads, 0, st>>>(rho, V_ext, vh, V_out, n0 * n1 * n2, h->d_epart);
