@@ -178,7 +178,9 @@ gint_status gint_force_stress(gint_handle* h, const double* V, const double* D, 
  * Every gradient is multiplied by *grad_E (a device scalar, the upstream gradient of a
  * reverse-mode chain; NULL means 1).  All pointers are device memory of the handle's device;
  * NULL outputs are skipped, at least one must be non-NULL.  V and D as for gint_force_stress
- * (D symmetric, canonical blocks read).  Errors as for gint_force_stress. */
+ * (D symmetric, canonical blocks read).  With a brick selection (gint_select_bricks) E and its
+ * gradients are those of the selected bricks' grid points (dE_dV is zero elsewhere).  Errors
+ * as for gint_force_stress. */
 gint_status gint_energy_grads(gint_handle* h, const double* V, const double* D, const double* grad_E, double* dE_dR,
                               double* dE_deps, double* dE_dV, double* dE_dD, double* E, gint_stream stream);
 

@@ -199,6 +199,10 @@ gint_status gint_energy_grads(gint_handle* h, const double* V, const double* D, 
         GINT_CUDA_TRY(cudaGetLastError());
     }
     if (dE_dV) {  // dE/dV_g = rho_g dV
+        const int64_t ng0 = (int64_t)h->grid.n[0] * h->grid.n[1] * h->grid.n[2];
+        // with a brick selection rho is written on the selected bricks only; E does not depend on V
+        // elsewhere, so those elements of the gradient are zero
+        if (h->selecting) GINT_CUDA_TRY(cudaMemsetAsync(dE_dV, 0, sizeof(double) * ng0, st));
         s = gint_rho(h, D, dE_dV, stream);
         if (s != GINT_OK) return s;
         const int64_t ng = (int64_t)h->grid.n[0] * h->grid.n[1] * h->grid.n[2];
