@@ -53,17 +53,23 @@ constexpr int kTcMaxSeg = 16;       // (row tile, column range) segments per bri
 
 // Sizes of the two forms (up to 640 padded orbital rows, 5 tiles of 128, in both).
 // Three-product form: pieces A_hi, A_lo, B_hi, B_lo over all rows; up to 1024
-// points per brick.  Exact form: pieces A_n, A_l1, A_l2 for the row tiles of
-// the current pass only (a pass of <= 256 output columns spans at most three
-// row tiles) and B_n, B_l1, B_l2 over all rows; up to 512 points per brick
-// (the integer products of 512 points stay below 2^23).
+// points per brick; two operand buffers (one chunk in flight per producer half).
+// Exact form: pieces A_n, A_l1, A_l2 for the row tiles of the current pass only
+// (a pass of <= 256 output columns spans at most three row tiles) and B_n, B_l1,
+// B_l2 for the columns the pass's segments read only (at most 256 rows, packed
+// in 16-row groups, plus one 16-row group that takes the stores of rows the pass
+// does not read); up to 512 points per brick (the integer products of 512 points
+// stay below 2^23); three operand buffers, so that a producer half rarely waits
+// for the MMAs of its previous chunk.
 template <bool kExact> struct TcCfg {
     static constexpr int kPieces = kExact ? 3 : 2;            // pieces per operand
     static constexpr int kRows = 640;
     static constexpr int kARows = kExact ? 384 : 640;         // rows held by an A piece
+    static constexpr int kBRows = kExact ? 256 + 16 : 640;    // rows held by a B piece
+    static constexpr int kBufs = kExact ? 3 : 2;              // operand buffers
     static constexpr int kPts = kExact ? 512 : 1024;
     static constexpr int kAPieceBytes = kARows * kTcChunk * 2;  // rows x 16 points x 2 B
-    static constexpr int kBPieceBytes = kRows * kTcChunk * 2;
+    static constexpr int kBPieceBytes = kBRows * kTcChunk * 2;
     static constexpr int kBOff = kPieces * kAPieceBytes;        // first B piece in a buffer
     static constexpr int kBufBytes = kPieces * (kAPieceBytes + kBPieceBytes);
     static constexpr int kPassCols = kExact ? 256 : 512;      // output columns per pass
@@ -87,7 +93,7 @@ struct TcArgs {
 
 template <bool kExact> struct TcSmem {
     using C = TcCfg<kExact>;
-    unsigned char buf[2][C::kBufBytes];
+    unsigned char buf[C::kBufs][C::kBufBytes];
     TcAtom at[kTcMaxAtoms];
     int pairblk[kTcMaxAtoms * (kTcMaxAtoms + 1) / 2];  // block of image pair a1 <= a2 (index a2 (a2+1)/2 + a1), -1 if none
     float4 pt[C::kPts];             // in-brick offset of each point (x, y, z) and 2^s V dV
@@ -95,6 +101,8 @@ template <bool kExact> struct TcSmem {
     unsigned char row_atom[C::kRows];
     unsigned char row_mu[C::kRows];
     unsigned short rowtab[C::kRows];  // byte offset of row r's 16-byte segment in a piece
+    unsigned short rowtabB[C::kRows]; // the same in a B piece (exact form: the pass's packed column rows)
+    short grp_pos[C::kRows / 16];     // exact form: packed position of each 16-column group the pass reads, -1 if none
     double row_s[C::kRows];           // exact form: [ylm_norm x] 2^qeu of row r (FP64)
     float row_f[C::kRows];            // exact form: 2^qeu of row r
     unsigned char need_list[kTcMaxAtoms];  // atom images with rows the current pass reads
@@ -104,8 +112,8 @@ template <bool kExact> struct TcSmem {
     int pass_first[kTcMaxSeg + 1];      // first segment of each pass
     int npass, nrow, ncol;
     float wmax[kTcThreads / 32];
-    uint64_t full[2];   // producers of buffer b arrived (kTcHalf arrivals)
-    uint64_t empty[2];  // MMAs reading buffer b completed (tcgen05.commit)
+    uint64_t full[C::kBufs];   // producers of buffer b arrived (kTcHalf arrivals)
+    uint64_t empty[C::kBufs];  // MMAs reading buffer b completed (tcgen05.commit)
     uint64_t done;      // all MMAs of the pass completed
     uint32_t tmem;
     int work;
@@ -233,22 +241,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(&S.full[0], kTcHalf);
-        tc::mbar_init(&S.full[1], kTcHalf);
-        tc::mbar_init(&S.empty[0], 1);
-        tc::mbar_init(&S.empty[1], 1);
+        for (int b = 0; b < C::kBufs; ++b) {
+            tc::mbar_init(&S.full[b], kTcHalf);
+            tc::mbar_init(&S.empty[b], 1);
+        }
         tc::mbar_init(&S.done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         S.abort = 0;
     }
     if (!kMulti) cell_setup(A.P);
-    for (int r = tid; r < C::kRows; r += kTcThreads) S.rowtab[r] = (unsigned short)((((r >> 3) * (kTcChunk / 8)) << 7) + ((r & 7) << 4));
+    for (int r = tid; r < C::kRows; r += kTcThreads) {
+        S.rowtab[r] = (unsigned short)((((r >> 3) * (kTcChunk / 8)) << 7) + ((r & 7) << 4));
+        if (!kExact) S.rowtabB[r] = S.rowtab[r];  // B holds every row
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = S.tmem;
     // completed phases of each barrier (every thread that waits on a barrier keeps its count)
-    uint32_t uses[2] = {0, 0};  // chunks produced into / issued from buffer b
+    // chunks of every pass so far (every thread keeps the same count): the chunk with global index G
+    // uses buffer G % kBufs, whose barriers' phase G / kBufs belongs to it
+    uint32_t gchunk = 0;
     uint32_t dones = 0;
     const bool issuer_warp = warp == kTcProdThreads / 32;
     const int half = warp >> 3;  // producer half (0 or 1) for warps 0-15
@@ -376,18 +389,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                 if (a1 <= a2) S.pairblk[pair_index(a1, a2)] = ld_stream_s32(pt + q);
             }
         }
-        // zero the padding rows [nrow, round128(nrow)) of both chunk buffers (B pieces; A pieces
-        // too in the three-product form, where A holds every row)
+        // three-product form: zero the padding rows [nrow, round128(nrow)) of the chunk buffers
+        // (A and B hold every row); the exact form zeroes its padding rows per pass
         const int nrow128 = (nrow + 127) & ~127;
-        for (int b = 0; b < 2; ++b)
-            for (int e = tid; e < (nrow128 - nrow) * kTcChunk; e += kTcThreads) {
-                const int r = nrow + e / kTcChunk, q = e % kTcChunk;
-                const int o = piece_off(r, q);
-                for (int pc = 0; pc < C::kPieces; ++pc) {
-                    *reinterpret_cast<unsigned short*>(&S.buf[b][kBOff + pc * kBP + o]) = 0;
-                    if (!kExact) *reinterpret_cast<unsigned short*>(&S.buf[b][pc * kAP + o]) = 0;
+        if (!kExact)
+            for (int b = 0; b < C::kBufs; ++b)
+                for (int e = tid; e < (nrow128 - nrow) * kTcChunk; e += kTcThreads) {
+                    const int r = nrow + e / kTcChunk, q = e % kTcChunk;
+                    const int o = piece_off(r, q);
+                    for (int pc = 0; pc < C::kPieces; ++pc) {
+                        *reinterpret_cast<unsigned short*>(&S.buf[b][kBOff + pc * kBP + o]) = 0;
+                        *reinterpret_cast<unsigned short*>(&S.buf[b][pc * kAP + o]) = 0;
+                    }
                 }
-            }
         __syncthreads();
 
         const int nchunks = g.bpad / kTcChunk;
@@ -417,25 +431,54 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                 }
                 if (lane == 0) S.n_need = __popcll(m);
             }
-            {
-                // zero A rows [max(nrow, a_lo), a_hi) (they may hold rows of the previous pass;
-                // every MMA of that pass has completed)
-                const int z0 = max(nrow, a_lo);
-                if (kExact)
-                    for (int b = 0; b < 2; ++b)
-                        for (int e = tid; e < (a_hi - z0) * kTcChunk; e += kTcThreads) {
-                            const int r = z0 - a_lo + e / kTcChunk, q = e % kTcChunk;
-                            const int o = piece_off(r, q);
-                            for (int pc = 0; pc < C::kPieces; ++pc) *reinterpret_cast<unsigned short*>(&S.buf[b][pc * kAP + o]) = 0;
-                        }
-                __syncthreads();
+            if (kExact && tid == 32) {
+                // packed B rows of this pass: the 16-column groups its segments read, in order
+                const int ng = S.ncol >> 4;
+                for (int gq = 0; gq < ng; ++gq) S.grp_pos[gq] = -1;
+                for (int sg = s0p; sg < s1p; ++sg)
+                    for (int gq = S.seg_c0[sg] >> 4; gq < (S.seg_c1[sg] >> 4); ++gq) S.grp_pos[gq] = 0;
+                int pos = 0;
+                for (int gq = 0; gq < ng; ++gq)
+                    if (S.grp_pos[gq] >= 0) S.grp_pos[gq] = (short)(pos++);
             }
+            if (kExact) {
+                __syncthreads();
+                // B row offsets of the pass (rows it does not read go to the spare group 256..271)
+                for (int r = tid; r < S.ncol; r += kTcThreads) {
+                    const int gp = S.grp_pos[r >> 4];
+                    const int pr = gp >= 0 ? (gp << 4) + (r & 15) : 256 + (r & 15);
+                    S.rowtabB[r] = (unsigned short)((((pr >> 3) * (kTcChunk / 8)) << 7) + ((pr & 7) << 4));
+                }
+                __syncthreads();
+                // zero A rows [max(nrow, a_lo), a_hi) and the packed B rows of the padding rows
+                // [nrow, ncol) in every buffer (they may hold rows of the previous pass; every MMA of
+                // that pass has completed); no producer writes them in this pass
+                const int z0 = max(nrow, a_lo);
+                for (int b = 0; b < C::kBufs; ++b) {
+                    for (int e = tid; e < (a_hi - z0) * kTcChunk; e += kTcThreads) {
+                        const int r = z0 - a_lo + e / kTcChunk, q = e % kTcChunk;
+                        const int o = piece_off(r, q);
+                        for (int pc = 0; pc < C::kPieces; ++pc) *reinterpret_cast<unsigned short*>(&S.buf[b][pc * kAP + o]) = 0;
+                    }
+                    for (int e = tid; e < (S.ncol - nrow) * kTcChunk; e += kTcThreads) {
+                        const int r = nrow + e / kTcChunk, q = e % kTcChunk;
+                        if (S.grp_pos[r >> 4] < 0) continue;
+                        const int o = S.rowtabB[r] + ((q >> 3) << 7) + ((q & 7) << 1);
+                        for (int pc = 0; pc < C::kPieces; ++pc)
+                            *reinterpret_cast<unsigned short*>(&S.buf[b][kBOff + pc * kBP + o]) = 0;
+                    }
+                }
+            }
+            __syncthreads();
             if (!issuer_warp) {
-                // ---- producers: half h fills buffer h with chunks c = h, h + 2, ...
-                const int b = half;
-                unsigned char* buf = S.buf[b];
-                for (int c = b; c < nchunks; c += 2) {
-                    if (uses[b] > 0 && !S.abort && !tc::mbar_wait(&S.empty[b], (uses[b] - 1) & 1, A.wait_limit))
+                // ---- producers: half h fills chunks c = h, h + 2, ... of the pass; chunk c (global
+                //      index G) goes to buffer G % kBufs once the MMAs of chunk G - kBufs have read it
+                for (int c = half; c < nchunks; c += 2) {
+                    const uint32_t G = gchunk + (uint32_t)c;
+                    const int b = (int)(G % C::kBufs);
+                    unsigned char* buf = S.buf[b];
+                    if (G >= (uint32_t)C::kBufs && !S.abort &&
+                        !tc::mbar_wait(&S.empty[b], ((G / C::kBufs) - 1) & 1, A.wait_limit))
                         atomicOr(&S.abort, 1);
                     // orbital values at the chunk's points, two points per item, for the atom
                     // images of need_list.  Item bits: [1:0] point pair within a half chunk,
@@ -464,7 +507,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                         const SpeciesFast& sf = S.spf[X.sp];
                         auto put2 = [&](int o, float va, float vb) {
                             const int r = rbase + o;
-                            const int offB = kBOff + S.rowtab[r] + qoff;
+                            const int offB = kBOff + S.rowtabB[r] + qoff;
                             auto st32 = [&](int off, uint32_t x) { *reinterpret_cast<uint32_t*>(&buf[off]) = x; };
                             if (kExact) {
                                 const float qi = exp2i(-sf.qeu[o]);  // unnormalised orbital values
@@ -490,7 +533,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                         if (!orbitals_fast2<!kExact>(sf, knot2, ax, ay, az, bx, by, bz, put2))
                             for (int o = 0; o < X.nw; ++o) {
                                 const int r = rbase + o;
-                                const int offB = kBOff + S.rowtab[r] + qoff;
+                                const int offB = kBOff + S.rowtabB[r] + qoff;
                                 const bool inA = r >= a_lo && r < a_hi;
                                 const int offA = inA ? S.rowtab[r - a_lo] + qoff : 0;
                                 for (int pc = 0; pc < C::kPieces; ++pc) {
@@ -501,15 +544,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                     }
                     tc::fence_async_smem();
                     tc::mbar_arrive(&S.full[b]);
-                    uses[b] += 1;
                 }
             } else if (lane == 0) {
                 // ---- issuer: one thread waits for each chunk, issues its MMAs and commits
                 const uint32_t lbo = 128, sbo = (kTcChunk / 8) * 128;
                 for (int c = 0; c < nchunks; ++c) {
-                    const int b = c & 1;
-                    if (!S.abort && !tc::mbar_wait(&S.full[b], uses[b] & 1, A.wait_limit)) atomicOr(&S.abort, 1);
-                    uses[b] += 1;
+                    const uint32_t G = gchunk + (uint32_t)c;
+                    const int b = (int)(G % C::kBufs);
+                    if (!S.abort && !tc::mbar_wait(&S.full[b], (G / C::kBufs) & 1, A.wait_limit)) atomicOr(&S.abort, 1);
                     tc::fence_after_sync();
                     const uint32_t base = tc::smem_u32(S.buf[b]);
                     // K-major operands: LBO = distance of K-adjacent core matrices (128 B),
@@ -524,7 +566,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                             for (int c0 = S.seg_c0[sg]; c0 < c_end; c0 += 256) {
                                 const int nn = min(256, c_end - c0);
                                 const uint32_t idesc = tc::idesc_f16(128, nn, Conv<H16>::bf16, 0, 0);
-                                const uint32_t pb0 = base + kBOff + (uint32_t)(c0 >> 3) * sbo;
+                                // B rows of columns [c0, c0 + nn): packed position in the exact form
+                                const int brow = kExact ? (S.grp_pos[c0 >> 4] << 4) : c0;
+                                const uint32_t pb0 = base + kBOff + (uint32_t)(brow >> 3) * sbo;
                                 const uint32_t pb1 = pb0 + kBP;
                                 const uint32_t pb2 = pb0 + 2 * kBP;  // exact form
                                 const uint32_t d = tmem + (uint32_t)(S.seg_tcol[sg] + c0 - S.seg_c0[sg]);
@@ -554,10 +598,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
             __syncwarp();
             if (!tc::mbar_wait(&S.done, dones & 1, kDrainPolls)) atomicOr(&S.abort, 1);
             dones += 1;
-            if (issuer_warp && lane != 0) {
-                // lanes 1-31 of the issuer warp keep the buffer counters in step with lane 0
-                for (int c = 0; c < nchunks; ++c) uses[c & 1] += 1;
-            }
+            gchunk += (uint32_t)nchunks;
             tc::fence_after_sync();
             __syncthreads();
             if (S.abort) break;
