@@ -3,6 +3,7 @@
 #include <algorithm>
 
 #include "gint_impl.cuh"
+#include "nvtx.cuh"
 
 namespace gint {
 gint_status simt_run(gint_handle* h, int which, bool fp32, const double* V, const double* D, double* out,
@@ -109,6 +110,7 @@ using namespace gint;
 extern "C" {
 
 gint_status gint_vlocal(gint_handle* h, const double* V, double* H, int accumulate, gint_stream stream) {
+    gint::NvtxRange nvtx_range_("gint_vlocal");
     set_error("");
     if (!h || !V || !H) { set_error("gint_vlocal: NULL argument"); return GINT_ERR_INVALID_ARG; }
     if (accumulate != 0 && accumulate != 1) { set_error("gint_vlocal: accumulate must be 0 or 1"); return GINT_ERR_INVALID_ARG; }
@@ -143,6 +145,7 @@ gint_status gint_check(const gint_handle* h) {
 }
 
 gint_status gint_rho(gint_handle* h, const double* D, double* rho, gint_stream stream) {
+    gint::NvtxRange nvtx_range_("gint_rho");
     set_error("");
     if (!h || !D || !rho) { set_error("gint_rho: NULL argument"); return GINT_ERR_INVALID_ARG; }
     bool fp32 = false;
@@ -161,6 +164,7 @@ gint_status gint_rho(gint_handle* h, const double* D, double* rho, gint_stream s
 
 gint_status gint_force_stress(gint_handle* h, const double* V, const double* D, double* F, double* sigma,
                               double* virial_atom, double* E, gint_stream stream) {
+    gint::NvtxRange nvtx_range_("gint_force_stress");
     set_error("");
     if (!h || !V || !D) { set_error("gint_force_stress: NULL argument"); return GINT_ERR_INVALID_ARG; }
     if (!F && !sigma && !virial_atom && !E) { set_error("gint_force_stress: no output requested"); return GINT_ERR_INVALID_ARG; }
@@ -177,6 +181,7 @@ gint_status gint_force_stress(gint_handle* h, const double* V, const double* D, 
 
 gint_status gint_energy_grads(gint_handle* h, const double* V, const double* D, const double* grad_E, double* dE_dR,
                               double* dE_deps, double* dE_dV, double* dE_dD, double* E, gint_stream stream) {
+    gint::NvtxRange nvtx_range_("gint_energy_grads");
     set_error("");
     if (!h || !V || !D) { set_error("gint_energy_grads: NULL argument"); return GINT_ERR_INVALID_ARG; }
     if (!dE_dR && !dE_deps && !dE_dV && !dE_dD && !E) { set_error("gint_energy_grads: no output requested"); return GINT_ERR_INVALID_ARG; }

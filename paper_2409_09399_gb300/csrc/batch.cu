@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "gint_impl.cuh"
+#include "nvtx.cuh"
 
 constexpr int kBranches = 4;
 
@@ -173,6 +174,7 @@ void gint_batch_destroy(gint_batch* b) {
 gint_status gint_batch_run(gint_batch* b, const double* const* V, const double* const* D, double* const* H,
                            double* const* rho, double* const* F, double* const* sigma, double* const* E,
                            gint_stream stream) {
+    gint::NvtxRange nvtx_range_("gint_batch_run");
     set_error("");
     if (!b || !V || !D) { set_error("gint_batch_run: NULL argument"); return GINT_ERR_INVALID_ARG; }
     const int n = b->n;

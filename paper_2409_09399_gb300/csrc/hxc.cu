@@ -19,6 +19,7 @@
 #include <cufft.h>
 
 #include "gint_impl.cuh"
+#include "nvtx.cuh"
 
 namespace gint {
 
@@ -265,6 +266,7 @@ using namespace gint;
 
 extern "C" gint_status gint_local_potential(gint_handle* h, const double* rho, const double* V_ext, double* V_out,
                                             double* V_H, double* energies, gint_stream stream) {
+    gint::NvtxRange nvtx_range_("gint_local_potential");
     set_error("");
     if (!h || !rho || !V_out) { set_error("gint_local_potential: NULL argument"); return GINT_ERR_INVALID_ARG; }
     const int64_t n0 = h->grid.n[0], n1 = h->grid.n[1], n2 = h->grid.n[2];

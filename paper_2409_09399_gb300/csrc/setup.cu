@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "gint_impl.cuh"
+#include "nvtx.cuh"
 
 namespace gint {
 
@@ -1049,6 +1050,7 @@ const char* gint_last_error(void) { return g_err; }
 
 gint_status gint_setup(int n_atoms, const double* pos, const int* species, const double* cell, int n_species,
                        const gint_species* sp, const int* grid, const gint_options* opt, gint_handle** out) {
+    gint::NvtxRange nvtx_range_("gint_setup");
     set_error("");
     if (!out) { set_error("out is NULL"); return GINT_ERR_INVALID_ARG; }
     *out = nullptr;
@@ -1206,6 +1208,7 @@ gint_status gint_sync(gint_handle* h, gint_stream stream) {
 
 gint_status gint_update_positions(gint_handle* h, const double* pos, const double* cell, int keep_pattern,
                                   int* pattern_changed) {
+    gint::NvtxRange nvtx_range_("gint_update_positions");
     set_error("");
     if (!h || !pos) { set_error("gint_update_positions: NULL argument"); return GINT_ERR_INVALID_ARG; }
     if (keep_pattern != 0 && keep_pattern != 1) { set_error("keep_pattern must be 0 or 1"); return GINT_ERR_INVALID_ARG; }
