@@ -43,24 +43,25 @@
 
 namespace gint {
 
-constexpr int kTcProdThreads = 512;   // 16 producer warps: two halves, one per chunk buffer
-constexpr int kTcHalf = kTcProdThreads / 2;
-constexpr int kTcThreads = kTcProdThreads + 32;  // + one MMA-issuing warp
+constexpr int kTcMaxThreads = 544;   // the larger of the two forms' CTAs (17 warps)
 constexpr int kTcChunk = 16;        // points per K chunk (one MMA K step)
 constexpr int kTcMaxAtoms = 64;     // atom images per brick
 constexpr int kTcMaxSpecies = 8;
 constexpr int kTcMaxSeg = 16;       // (row tile, column range) segments per brick
 
 // Sizes of the two forms (up to 640 padded orbital rows, 5 tiles of 128, in both).
+// Each form has one group of producer warps per operand buffer (a group fills
+// every kGroups-th chunk), plus one MMA-issuing warp.
 // Three-product form: pieces A_hi, A_lo, B_hi, B_lo over all rows; up to 1024
-// points per brick; two operand buffers (one chunk in flight per producer half).
+// points per brick; two operand buffers, two groups of 8 warps (17 warps).
 // Exact form: pieces A_n, A_l1, A_l2 for the row tiles of the current pass only
 // (a pass of <= 256 output columns spans at most three row tiles) and B_n, B_l1,
 // B_l2 for the columns the pass's segments read only (at most 256 rows, packed
 // in 16-row groups, plus one 16-row group that takes the stores of rows the pass
 // does not read); up to 512 points per brick (the integer products of 512 points
-// stay below 2^23); three operand buffers, so that a producer half rarely waits
-// for the MMAs of its previous chunk.
+// stay below 2^23); three operand buffers and three groups of 5 warps (16 warps
+// with the issuer, so up to 128 registers a thread): three chunks are produced
+// at once, and a group waits for the MMAs of its own previous chunk only.
 template <bool kExact> struct TcCfg {
     static constexpr int kPieces = kExact ? 3 : 2;            // pieces per operand
     static constexpr int kRows = 640;
@@ -73,6 +74,11 @@ template <bool kExact> struct TcCfg {
     static constexpr int kBOff = kPieces * kAPieceBytes;        // first B piece in a buffer
     static constexpr int kBufBytes = kPieces * (kAPieceBytes + kBPieceBytes);
     static constexpr int kPassCols = kExact ? 256 : 512;      // output columns per pass
+    static constexpr int kGroups = kBufs;                     // producer groups, one chunk in flight each
+    static constexpr int kGroupWarps = kExact ? 5 : 8;
+    static constexpr int kGroupThreads = 32 * kGroupWarps;
+    static constexpr int kProdWarps = kGroups * kGroupWarps;
+    static constexpr int kThreads = 32 * (kProdWarps + 1);    // + the MMA-issuing warp
 };
 
 struct TcAtom {
@@ -111,8 +117,8 @@ template <bool kExact> struct TcSmem {
     short seg_c0[kTcMaxSeg], seg_c1[kTcMaxSeg], seg_tcol[kTcMaxSeg];
     int pass_first[kTcMaxSeg + 1];      // first segment of each pass
     int npass, nrow, ncol;
-    float wmax[kTcThreads / 32];
-    uint64_t full[C::kBufs];   // producers of buffer b arrived (kTcHalf arrivals)
+    float wmax[kTcMaxThreads / 32];
+    uint64_t full[C::kBufs];   // producers of buffer b arrived (kGroupThreads arrivals)
     uint64_t empty[C::kBufs];  // MMAs reading buffer b completed (tcgen05.commit)
     uint64_t done;      // all MMAs of the pass completed
     uint32_t tmem;
@@ -208,12 +214,13 @@ __device__ __forceinline__ double f2d_exact(float x) {
 // kMulti: the work queue spans the bricks of many cells (a batch, MultiArgs);
 // the problem, V and H of an item come from its cell's CellJob.
 template <typename H16, bool kExact, bool kMulti>
-__global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_constant__ TcArgs A, const double* V_in, double* H_in,
+__global__ void __launch_bounds__(TcCfg<kExact>::kThreads, 1) k_vlocal_tc(const __grid_constant__ TcArgs A, const double* V_in, double* H_in,
                                                                 const __grid_constant__ MultiArgs M) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem<kExact>& S = *reinterpret_cast<TcSmem<kExact>*>(smem_raw);
     using C = TcCfg<kExact>;
     constexpr int kPassCols = C::kPassCols;
+    constexpr int kTcThreads = C::kThreads;
     constexpr int kAP = C::kAPieceBytes, kBP = C::kBPieceBytes, kBOff = C::kBOff;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const Problem* Pc = &A.P;  // problem, V and H of the current item
@@ -242,7 +249,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
     }
     if (tid == 0) {
         for (int b = 0; b < C::kBufs; ++b) {
-            tc::mbar_init(&S.full[b], kTcHalf);
+            tc::mbar_init(&S.full[b], C::kGroupThreads);
             tc::mbar_init(&S.empty[b], 1);
         }
         tc::mbar_init(&S.done, 1);
@@ -263,9 +270,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
     // uses buffer G % kBufs, whose barriers' phase G / kBufs belongs to it
     uint32_t gchunk = 0;
     uint32_t dones = 0;
-    const bool issuer_warp = warp == kTcProdThreads / 32;
-    const int half = warp >> 3;  // producer half (0 or 1) for warps 0-15
-    const int lt = tid & (kTcHalf - 1);
+    const bool issuer_warp = warp == C::kProdWarps;
+    const int grp = warp / C::kGroupWarps;  // producer group of warps 0 .. kProdWarps - 1
+    const int lt = tid - grp * C::kGroupThreads;
 
     for (;;) {
         if (tid == 0) S.work = atomicAdd(A.counter, 1);
@@ -471,9 +478,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
             }
             __syncthreads();
             if (!issuer_warp) {
-                // ---- producers: half h fills chunks c = h, h + 2, ... of the pass; chunk c (global
-                //      index G) goes to buffer G % kBufs once the MMAs of chunk G - kBufs have read it
-                for (int c = half; c < nchunks; c += 2) {
+                // ---- producers: group g fills chunks c = g, g + kGroups, ... of the pass; chunk c
+                //      (global index G) goes to buffer G % kBufs once the MMAs of chunk G - kBufs
+                //      have read it
+                for (int c = grp; c < nchunks; c += C::kGroups) {
                     const uint32_t G = gchunk + (uint32_t)c;
                     const int b = (int)(G % C::kBufs);
                     unsigned char* buf = S.buf[b];
@@ -481,16 +489,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
                         !tc::mbar_wait(&S.empty[b], ((G / C::kBufs) - 1) & 1, A.wait_limit))
                         atomicOr(&S.abort, 1);
                     // orbital values at the chunk's points, two points per item, for the atom
-                    // images of need_list.  Item bits: [1:0] point pair within a half chunk,
-                    // [4:2] list entry within a group of 8, [5] half chunk, [6..] group; so a
-                    // warp stores 8 atoms (distinct rows mod 8) x 4 point pairs of the same
-                    // 16-byte row segment half: 32 different banks.
+                    // images of need_list: 8 items (point pairs) per image.  Items of the full
+                    // blocks of 8 images: bits [1:0] point pair within a half chunk, [4:2] list
+                    // entry within the block, [5] half chunk, [6..] block; so a warp stores 8
+                    // atoms (distinct rows mod 8) x 4 point pairs of the same 16-byte row
+                    // segment half: 32 different banks.  The r < 8 images of the last block take
+                    // items j = qp r + (k mod 8) (at most two-way bank conflicts).
                     const int n_need = S.n_need;
-                    const int n_items = ((n_need + 7) >> 3) << 6;
-                    for (int item = lt; item < n_items; item += kTcHalf) {
-                        const int k = ((item >> 6) << 3) | ((item >> 2) & 7);
-                        const int qp = (((item >> 5) & 1) << 2) | (item & 3);
-                        if (k >= n_need) continue;
+                    const int n_full = (n_need >> 3) << 6;
+                    const int r_last = n_need & 7;
+                    const int n_items = 8 * n_need;
+                    for (int item = lt; item < n_items; item += C::kGroupThreads) {
+                        int k, qp;
+                        if (item < n_full) {
+                            k = ((item >> 6) << 3) | ((item >> 2) & 7);
+                            qp = (((item >> 5) & 1) << 2) | (item & 3);
+                        } else {
+                            const int j = item - n_full;
+                            qp = j / r_last;
+                            k = (n_full >> 3) + (j - qp * r_last);
+                        }
                         const TcAtom& X = S.at[S.need_list[k]];
                         const int q = 2 * qp;
                         const int p = c * kTcChunk + q;
@@ -602,9 +620,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
             tc::fence_after_sync();
             __syncthreads();
             if (S.abort) break;
-            // ---- epilogue: producer warps; lanes = rows (lane group warp & 3), the four warps of a
-            //      lane group take every fourth 16-column group
-            if (!issuer_warp) {
+            // ---- epilogue: warps 0-15 (the exact form's issuing warp among them); lanes = rows
+            //      (lane group warp & 3), the four warps of a lane group take every fourth
+            //      16-column group
+            if (warp < 16) {
                 const int lane_base = (warp & 3) * 32;
                 const float sinv = S.scale_inv;
                 for (int sg = s0p; sg < s1p; ++sg) {
@@ -680,6 +699,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vlocal_tc(const __grid_consta
 }
 
 template <bool kExact> size_t tc_smem_bytes() { return sizeof(TcSmem<kExact>) + 1024; }
+template <bool kExact> constexpr int tc_threads() { return TcCfg<kExact>::kThreads; }
 
 // Exact form: multiply every canonical H block by the harmonic normalisation of
 // its row and column orbitals (FP64, once per element rather than once per brick).
@@ -731,7 +751,7 @@ gint_status tc_vlocal(gint_handle* h, int form, const double* V, double* H, int 
     do {                                                                                                       \
         GINT_CUDA_TRY(cudaFuncSetAttribute(k_vlocal_tc<H16, X, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                            (int)smem));                                                        \
-        k_vlocal_tc<H16, X, false><<<h->sm_count, kTcThreads, smem, st>>>(A, V, H, MultiArgs{});              \
+        k_vlocal_tc<H16, X, false><<<h->sm_count, tc_threads<X>(), smem, st>>>(A, V, H, MultiArgs{});              \
     } while (0)
     if (form == 1) GINT_LAUNCH_VL(__nv_bfloat16, false);
     else if (form == 2) GINT_LAUNCH_VL(__half, true);
@@ -769,7 +789,7 @@ gint_status tc_vlocal_multi(int form, const MultiArgs& M, int* counter, int sm_c
     do {                                                                                                       \
         GINT_CUDA_TRY(cudaFuncSetAttribute(k_vlocal_tc<H16, X, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                            (int)smem));                                                        \
-        k_vlocal_tc<H16, X, true><<<sm_count, kTcThreads, smem, st>>>(A, nullptr, nullptr, M);                 \
+        k_vlocal_tc<H16, X, true><<<sm_count, tc_threads<X>(), smem, st>>>(A, nullptr, nullptr, M);                 \
     } while (0)
     if (form == 1) GINT_LAUNCH_VLM(__nv_bfloat16, false);
     else if (form == 2) GINT_LAUNCH_VLM(__half, true);
