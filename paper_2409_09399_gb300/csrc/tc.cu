@@ -59,9 +59,10 @@ constexpr int kTcMaxSeg = 16;       // (row tile, column range) segments per bri
 // B_l2 for the columns the pass's segments read only (at most 256 rows, packed
 // in 16-row groups, plus one 16-row group that takes the stores of rows the pass
 // does not read); up to 512 points per brick (the integer products of 512 points
-// stay below 2^23); three operand buffers and three groups of 5 warps (16 warps
-// with the issuer, so up to 128 registers a thread): three chunks are produced
-// at once, and a group waits for the MMAs of its own previous chunk only.
+// stay below 2^23); three operand buffers and three groups of 6 warps (19 warps
+// with the issuer): three chunks are produced at once, a group waits for the
+// MMAs of its own previous chunk only, and a pass of up to 24 atom images takes
+// one item per thread.
 template <bool kExact> struct TcCfg {
     static constexpr int kPieces = kExact ? 3 : 2;            // pieces per operand
     static constexpr int kRows = 640;
@@ -75,7 +76,7 @@ template <bool kExact> struct TcCfg {
     static constexpr int kBufBytes = kPieces * (kAPieceBytes + kBPieceBytes);
     static constexpr int kPassCols = kExact ? 256 : 512;      // output columns per pass
     static constexpr int kGroups = kBufs;                     // producer groups, one chunk in flight each
-    static constexpr int kGroupWarps = kExact ? 5 : 8;
+    static constexpr int kGroupWarps = kExact ? 6 : 8;
     static constexpr int kGroupThreads = 32 * kGroupWarps;
     static constexpr int kProdWarps = kGroups * kGroupWarps;
     static constexpr int kThreads = 32 * (kProdWarps + 1);    // + the MMA-issuing warp
@@ -620,9 +621,8 @@ __global__ void __launch_bounds__(TcCfg<kExact>::kThreads, 1) k_vlocal_tc(const 
             tc::fence_after_sync();
             __syncthreads();
             if (S.abort) break;
-            // ---- epilogue: warps 0-15 (the exact form's issuing warp among them); lanes = rows
-            //      (lane group warp & 3), the four warps of a lane group take every fourth
-            //      16-column group
+            // ---- epilogue: warps 0-15; lanes = rows (lane group warp & 3), the four warps of a
+            //      lane group take every fourth 16-column group
             if (warp < 16) {
                 const int lane_base = (warp & 3) * 32;
                 const float sinv = S.scale_inv;

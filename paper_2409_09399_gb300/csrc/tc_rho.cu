@@ -44,10 +44,19 @@
 namespace gint {
 
 namespace {
-constexpr int kProdWarps = 8;                    // orbital-value producers and epilogue
-constexpr int kCopyWarp = kProdWarps;            // bulk copies of B
-constexpr int kMmaWarp = kProdWarps + 1;         // MMA issue (one thread)
-constexpr int kThreads = 32 * kProdWarps + 64;
+// Warp roles: producer/epilogue warps in groups of 8 (a group fills every
+// kGroups-th K step, 2 images x 128 points, one thread per (image, point)),
+// then one warp for the bulk copies of B and one for the MMA issue.  rho in
+// the exact form runs two groups (two steps produced at once); the force, whose
+// epilogue needs 168 registers a thread, and the three-product form, whose
+// B buffers leave no shared memory for the larger epilogue staging, one.
+template <bool kForce, bool kExact> struct RfWarps {
+    static constexpr int kProdWarps = (!kForce && kExact) ? 16 : 8;
+    static constexpr int kGroups = kProdWarps / 8;
+    static constexpr int kCopyWarp = kProdWarps;      // bulk copies of B
+    static constexpr int kMmaWarp = kProdWarps + 1;   // MMA issue (one thread)
+    static constexpr int kThreads = 32 * kProdWarps + 64;
+};
 constexpr int kMaxAtoms = 64;
 constexpr int kMaxCols = 512;            // TMEM columns (packed orbitals of one M-tile)
 // A pieces (128 points x 16 orbital slots) are MN-major: core matrix (point group
@@ -75,7 +84,7 @@ struct Atom {
     int t[3];
 };
 
-template <bool kExact> struct Smem {
+template <bool kExact, int kPW> struct Smem {
     using C = RfCfg<kExact>;
     unsigned char A[2][2][C::kPieces * kAPiece];   // [buffer][image of the step][pieces]
     unsigned char B[2][2][C::kPieces * C::kBPiece];
@@ -83,9 +92,9 @@ template <bool kExact> struct Smem {
     int pairblk[kMaxAtoms * kMaxAtoms];  // block (I_a2, I_a1, T_a1 - T_a2) for K image a1, N image a2; -1 if none
     float W2[kMaxBrickPts];              // 2 V dV (force)
     double red[kMaxAtoms][13];           // per-image F(3), virial(9), energy
-    float Gst[8][32][17];                // epilogue: G values of one image per lane (padded row)
+    float Gst[kPW][32][17];              // epilogue: G values of one image per lane (padded row)
     float rho_part[128];                 // rho of the tile's points over earlier column groups
-    float rho_half[128];                 // partial rho from warps 4-7
+    float rho_q[kPW / 4 - 1][128];       // partial rho of warps 4 q .. 4 q + 3, q >= 1
     float qd[kMaxCols];                  // exact form: G scale 2^(qa + qD) of each output column of the group
     SpeciesFast spf[kMaxSpecies];
     unsigned char act[kMaxAtoms];
@@ -97,8 +106,8 @@ template <bool kExact> struct Smem {
     int work, abort, nact, ncols;
 };
 
-static_assert(sizeof(Smem<false>) + 1024 <= 232448, "shared memory of the rho/force kernel exceeds 227 KB");
-static_assert(sizeof(Smem<true>) + 1024 <= 232448, "shared memory of the exact rho/force kernel exceeds 227 KB");
+static_assert(sizeof(Smem<false, 8>) + 1024 <= 232448, "shared memory of the rho/force kernel exceeds 227 KB");
+static_assert(sizeof(Smem<true, 16>) + 1024 <= 232448, "shared memory of the exact rho/force kernel exceeds 227 KB");
 
 // Exact form: s = n + l1 + l2 (n = rint(s), |s| <= 128; l1, l2 fp16 pieces of s - n).
 __device__ __forceinline__ void fix_split3(float s, unsigned short& n16, unsigned short& l1, unsigned short& l2) {
@@ -228,11 +237,14 @@ __global__ void k_format_d(Problem P, const int32_t* mirror, const int* nw_atom,
 // kMulti: the work queue spans the bricks of many cells (a batch, MultiArgs); the
 // problem and the buffers of an item come from its cell's CellJob.
 template <typename H16, bool kForce, bool kExact, bool kMulti>
-__global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_constant__ CellJob J_in, int* counter, const __grid_constant__ MultiArgs M,
+__global__ void __launch_bounds__(RfWarps<kForce, kExact>::kThreads, 1) k_rhoforce_tc(const __grid_constant__ CellJob J_in, int* counter, const __grid_constant__ MultiArgs M,
                                                                  long wait_limit) {
     constexpr int kCols = kExact ? kMaxCols / 2 : kMaxCols;  // output columns of one column group
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    Smem<kExact>& S = *reinterpret_cast<Smem<kExact>*>(smem_raw);
+    using Wr = RfWarps<kForce, kExact>;
+    constexpr int kProdWarps = Wr::kProdWarps, kCopyWarp = Wr::kCopyWarp, kMmaWarp = Wr::kMmaWarp;
+    constexpr int kThreads = Wr::kThreads;
+    Smem<kExact, kProdWarps>& S = *reinterpret_cast<Smem<kExact, kProdWarps>*>(smem_raw);
     using C = RfCfg<kExact>;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const CellJob* Jc = &J_in;  // problem and buffers of the current item
@@ -244,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
     }
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
-            tc::mbar_init(&S.full[b], 32 * kProdWarps);
+            tc::mbar_init(&S.full[b], 256);  // one producer group
             tc::mbar_init(&S.empty[b], 1);
             tc::mbar_init(&S.bfull[b], 1);
         }
@@ -268,6 +280,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
     };
     if (kExact && !kMulti) set_qa(J_in.P);
     uint32_t uses[2] = {0, 0};  // steps that used buffer b (every thread counts them)
+    int a_rows0 = 16, a_rows1 = 16;  // producers: rows of their A column in buffer 0 / 1 that may be non-zero
     uint32_t dones = 0;         // completed phases of done
     uint32_t bissue[2] = {0, 0};  // copy warp: bulk-copy phases started per buffer
     uint32_t chunk = 0;  // global chunk counter (buffer parity)
@@ -379,18 +392,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
             // of step s + 1 start as soon as the MMAs of step s - 1 complete.
             const int nsteps = (nact + 1) >> 1;
             if (warp < kProdWarps) {
-                const int j = tid >> 7, pl = tid & 127;
+                // group grp fills steps grp, grp + kGroups, ...; the previous use of a step's
+                // buffer is then the group's own previous step (kGroups = 2) or the step before
+                const int grp = warp >> 3, j = (tid >> 7) & 1, pl = tid & 127;
                 for (int st = 0; st < nsteps; ++st) {
                     const int b = (chunk + st) & 1, k = 2 * st;
                     const int nk = min(2, nact - k);
+                    if (Wr::kGroups > 1 && st % Wr::kGroups != grp) {
+                        uses[b] += 1;
+                        continue;
+                    }
                     if (uses[b] > 0 && !tc::mbar_wait(&S.empty[b], (uses[b] - 1) & 1, wait_limit)) atomicOr(&S.abort, 1);
                     if (j < nk && !S.abort) {
                         const Atom& X = S.at[S.act[k + j]];
                         const int p = mt * 128 + pl;
                         unsigned char* A0 = S.A[b][j];
-                        for (int o = X.nw; o < 16; ++o)
+                        // slot rows [nw, 16) must be zero; rows at or above the thread's last nw
+                        // in this buffer already are (each thread owns one (slot, point) column)
+                        const int dirty = b ? a_rows1 : a_rows0;
+                        for (int o = X.nw; o < dirty; ++o)
                             for (int pc = 0; pc < C::kPieces; ++pc)
                                 *reinterpret_cast<unsigned short*>(A0 + pc * kAPiece + amn(pl, o)) = 0;
+                        if (b) a_rows1 = X.nw; else a_rows0 = X.nw;
                         bool inside = false;
                         if (p < g.bpts) {
                             float fx, fy, fz;
@@ -512,7 +535,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
                 float fx = 0.f, fy = 0.f, fz = 0.f;
                 if (p < g.bpts) point_offset(g, p, fx, fy, fz);
                 float rho_p = (cg0 == 0 || warp >= 4) ? 0.f : S.rho_part[pl];
-                for (int j = cg0 + (warp >> 2); warp < kProdWarps && j < cg1; j += 2) {
+                for (int j = cg0 + (warp >> 2); warp < kProdWarps && j < cg1; j += kProdWarps / 4) {
                     const int a2 = S.act[j];
                     const Atom& Y = S.at[a2];
                     const int c0 = 16 * (j - cg0);  // the image's slot
@@ -563,11 +586,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhoforce_tc(const __grid_consta
                         if (!(lane & 1) && q < 13) atomicAdd(&S.red[j][q], (double)tot);
                     }
                 }
-                if (warp >= 4 && warp < kProdWarps) S.rho_half[pl] = rho_p;
+                if (warp >= 4 && warp < kProdWarps) S.rho_q[(warp >> 2) - 1][pl] = rho_p;
                 tc::fence_before_sync();
                 __syncthreads();
                 if (warp < 4) {
-                    rho_p += S.rho_half[pl];
+#pragma unroll
+                    for (int q = 0; q < kProdWarps / 4 - 1; ++q) rho_p += S.rho_q[q][pl];
                     S.rho_part[pl] = rho_p;
                     if (!kForce && pv && cg1 == nact) rho[((int64_t)g0 * g.n[1] + g1) * g.n[2] + g2] = (double)rho_p;
                 }
@@ -681,12 +705,12 @@ static gint_status launch_rf(int form, bool force, const CellJob& J, const Multi
                              int sm_count, long wait_limit, cudaStream_t st) {
     const bool exact = form == 2;
     GINT_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
-    const size_t smem = (exact ? sizeof(Smem<true>) : sizeof(Smem<false>)) + 1024;
 #define GINT_LAUNCH_RF(H16, F, X, MU)                                                                          \
     do {                                                                                                        \
+        const size_t smem = sizeof(Smem<X, RfWarps<F, X>::kProdWarps>) + 1024;                                  \
         GINT_CUDA_TRY(cudaFuncSetAttribute(k_rhoforce_tc<H16, F, X, MU>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                            (int)smem));                                                         \
-        k_rhoforce_tc<H16, F, X, MU><<<sm_count, kThreads, smem, st>>>(J, counter, M, wait_limit);               \
+        k_rhoforce_tc<H16, F, X, MU><<<sm_count, RfWarps<F, X>::kThreads, smem, st>>>(J, counter, M, wait_limit);   \
     } while (0)
 #define GINT_LAUNCH_RF2(H16, X, MU) \
     do { if (force) GINT_LAUNCH_RF(H16, true, X, MU); else GINT_LAUNCH_RF(H16, false, X, MU); } while (0)
