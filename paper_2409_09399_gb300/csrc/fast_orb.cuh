@@ -255,9 +255,12 @@ __device__ __forceinline__ void put_l2(int o, float ua, float ub, float ax, floa
 // kNorm = false the harmonic normalisation ylm_norm(l, m) is left out (the
 // caller applies it in FP64).  Species of the s, s', p, p', d shape take an
 // unrolled path that loads the knots of all five radial functions at once.
-template <bool kNorm = true, typename Put2>
+// pre() runs once the first knot loads are issued and before the first put2,
+// so a caller can wait there for its output buffer while the loads are in flight.
+template <bool kNorm = true, typename Put2, typename Pre>
 __device__ __forceinline__ bool orbitals_fast2(const SpeciesFast& s, const float2* __restrict__ knot, float ax,
-                                               float ay, float az, float bx, float by, float bz, Put2&& put2) {
+                                               float ay, float az, float bx, float by, float bz, Put2&& put2,
+                                               Pre&& pre) {
     const float r2a = ax * ax + ay * ay + az * az;
     const float r2b = bx * bx + by * by + bz * bz;
     const bool ina = r2a < s.rc2, inb = r2b < s.rc2;
@@ -291,6 +294,7 @@ __device__ __forceinline__ bool orbitals_fast2(const SpeciesFast& s, const float
             pa[j] = ld_knot(kna + j); qa[j] = ld_knot(kna + 5 + j);
             pb[j] = ld_knot(knb + j); qb[j] = ld_knot(knb + 5 + j);
         }
+        pre();  // the knot loads are in flight
         float ua, ub;
         radial(0, pa[0], qa[0], pb[0], qb[0], ua, ub);
         put_l2<0, kNorm>(0, ua, ub, ax, ay, az, bx, by, bz, put2);
@@ -308,6 +312,7 @@ __device__ __forceinline__ bool orbitals_fast2(const SpeciesFast& s, const float
     // stored, so their latency overlaps that work
     float2 pa = make_float2(0.f, 0.f), qa = pa, pb = pa, qb = pa;
     if (nr > 0) { pa = ld_knot(kna); qa = ld_knot(kna + nr); pb = ld_knot(knb); qb = ld_knot(knb + nr); }
+    pre();
     for (int j = 0; j < nr; ++j) {
         float2 pa1 = pa, qa1 = qa, pb1 = pb, qb1 = qb;
         if (j + 1 < nr) {
@@ -325,6 +330,11 @@ __device__ __forceinline__ bool orbitals_fast2(const SpeciesFast& s, const float
         pa = pa1; qa = qa1; pb = pb1; qb = qb1;
     }
     return true;
+}
+template <bool kNorm = true, typename Put2>
+__device__ __forceinline__ bool orbitals_fast2(const SpeciesFast& s, const float2* __restrict__ knot, float ax,
+                                               float ay, float az, float bx, float by, float bz, Put2&& put2) {
+    return orbitals_fast2<kNorm>(s, knot, ax, ay, az, bx, by, bz, put2, [] {});
 }
 
 }  // namespace gint

@@ -486,9 +486,16 @@ __global__ void __launch_bounds__(TcCfg<kExact>::kThreads, 1) k_vlocal_tc(const 
                     const uint32_t G = gchunk + (uint32_t)c;
                     const int b = (int)(G % C::kBufs);
                     unsigned char* buf = S.buf[b];
-                    if (G >= (uint32_t)C::kBufs && !S.abort &&
-                        !tc::mbar_wait(&S.empty[b], ((G / C::kBufs) - 1) & 1, A.wait_limit))
-                        atomicOr(&S.abort, 1);
+                    // the buffer is free once the MMAs of chunk G - kBufs completed; a thread waits
+                    // for that only before its first store (its first item's knot loads are then in
+                    // flight) or before it arrives
+                    bool freed = G < (uint32_t)C::kBufs;
+                    auto ensure_free = [&]() {
+                        if (freed) return;
+                        if (!S.abort && !tc::mbar_wait(&S.empty[b], ((G / C::kBufs) - 1) & 1, A.wait_limit))
+                            atomicOr(&S.abort, 1);
+                        freed = true;
+                    };
                     // orbital values at the chunk's points, two points per item, for the atom
                     // images of need_list: 8 items (point pairs) per image.  Items of the full
                     // blocks of 8 images: bits [1:0] point pair within a half chunk, [4:2] list
@@ -549,7 +556,8 @@ __global__ void __launch_bounds__(TcCfg<kExact>::kThreads, 1) k_vlocal_tc(const 
                                 st32(offB, bh); st32(offB + kBP, bl);
                             }
                         };
-                        if (!orbitals_fast2<!kExact>(sf, knot2, ax, ay, az, bx, by, bz, put2))
+                        if (!orbitals_fast2<!kExact>(sf, knot2, ax, ay, az, bx, by, bz, put2, ensure_free)) {
+                            ensure_free();
                             for (int o = 0; o < X.nw; ++o) {
                                 const int r = rbase + o;
                                 const int offB = kBOff + S.rowtabB[r] + qoff;
@@ -560,7 +568,9 @@ __global__ void __launch_bounds__(TcCfg<kExact>::kThreads, 1) k_vlocal_tc(const 
                                     if (inA) *reinterpret_cast<uint32_t*>(&buf[offA + pc * kAP]) = 0u;
                                 }
                             }
+                        }
                     }
+                    ensure_free();
                     tc::fence_async_smem();
                     tc::mbar_arrive(&S.full[b]);
                 }
