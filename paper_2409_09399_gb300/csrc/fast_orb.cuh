@@ -127,10 +127,11 @@ __device__ __forceinline__ void put_l(int o, float u, float a, float dx, float d
 // displacement d (the gradient arguments are meaningful only with kGrad);
 // returns false (no calls) when |d| >= rc.  Species of the s, s', p, p', d
 // shape take an unrolled path that loads the knots of all five radial
-// functions at once.
-template <bool kGrad, typename Put>
+// functions at once.  pre() runs once the first knot loads are issued and
+// before the first put.
+template <bool kGrad, typename Put, typename Pre>
 __device__ __forceinline__ bool orbitals_fast(const SpeciesFast& s, const float2* __restrict__ knot, float dx,
-                                              float dy, float dz, Put&& put) {
+                                              float dy, float dz, Put&& put, Pre&& pre) {
     const float r2 = dx * dx + dy * dy + dz * dz;
     if (r2 >= s.rc2) return false;
     const bool tiny = r2 < 1e-20f;
@@ -183,6 +184,7 @@ __device__ __forceinline__ bool orbitals_fast(const SpeciesFast& s, const float2
         float2 y0[5], y1[5];
 #pragma unroll
         for (int j = 0; j < 5; ++j) { y0[j] = ld_knot(kn + j); y1[j] = ld_knot(kn + 5 + j); }
+        pre();  // the knot loads are in flight
         radial(L0{}, 0, y0[0], y1[0]);
         radial(L0{}, 1, y0[1], y1[1]);
         radial(L1{}, 2, y0[2], y1[2]);
@@ -194,6 +196,7 @@ __device__ __forceinline__ bool orbitals_fast(const SpeciesFast& s, const float2
     // values of j are formed, so their latency overlaps that work
     float2 y0n = make_float2(0.f, 0.f), y1n = y0n;
     if (nr > 0) { y0n = ld_knot(kn); y1n = ld_knot(kn + nr); }
+    pre();
     for (int j = 0; j < nr; ++j) {
         const float2 y0 = y0n, y1 = y1n;
         if (j + 1 < nr) { y0n = ld_knot(kn + j + 1); y1n = ld_knot(kn + nr + j + 1); }
@@ -205,6 +208,12 @@ __device__ __forceinline__ bool orbitals_fast(const SpeciesFast& s, const float2
         else radial(L3{}, o, y0, y1);
     }
     return true;
+}
+
+template <bool kGrad, typename Put>
+__device__ __forceinline__ bool orbitals_fast(const SpeciesFast& s, const float2* __restrict__ knot, float dx,
+                                              float dy, float dz, Put&& put) {
+    return orbitals_fast<kGrad>(s, knot, dx, dy, dz, put, [] {});
 }
 
 }  // namespace gint

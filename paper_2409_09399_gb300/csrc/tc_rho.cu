@@ -402,18 +402,19 @@ __global__ void __launch_bounds__(RfWarps<kForce, kExact>::kThreads, 1) k_rhofor
                         uses[b] += 1;
                         continue;
                     }
-                    if (uses[b] > 0 && !tc::mbar_wait(&S.empty[b], (uses[b] - 1) & 1, wait_limit)) atomicOr(&S.abort, 1);
+                    // buffer b is free once the MMAs of its previous step completed; a thread
+                    // waits for that before its first store (with its knot loads in flight) or
+                    // before it arrives
+                    bool freed = uses[b] == 0;
+                    auto ensure_free = [&]() {
+                        if (freed) return;
+                        if (!tc::mbar_wait(&S.empty[b], (uses[b] - 1) & 1, wait_limit)) atomicOr(&S.abort, 1);
+                        freed = true;
+                    };
                     if (j < nk && !S.abort) {
                         const Atom& X = S.at[S.act[k + j]];
                         const int p = mt * 128 + pl;
                         unsigned char* A0 = S.A[b][j];
-                        // slot rows [nw, 16) must be zero; rows at or above the thread's last nw
-                        // in this buffer already are (each thread owns one (slot, point) column)
-                        const int dirty = b ? a_rows1 : a_rows0;
-                        for (int o = X.nw; o < dirty; ++o)
-                            for (int pc = 0; pc < C::kPieces; ++pc)
-                                *reinterpret_cast<unsigned short*>(A0 + pc * kAPiece + amn(pl, o)) = 0;
-                        if (b) a_rows1 = X.nw; else a_rows0 = X.nw;
                         bool inside = false;
                         if (p < g.bpts) {
                             float fx, fy, fz;
@@ -429,13 +430,22 @@ __global__ void __launch_bounds__(RfWarps<kForce, kExact>::kThreads, 1) k_rhofor
                                 *reinterpret_cast<unsigned short*>(A0 + kAPiece + amn(pl, o)) = lo;
                                 if (kExact) *reinterpret_cast<unsigned short*>(A0 + 2 * kAPiece + amn(pl, o)) = l2;
                             };
-                            inside = orbitals_fast<false>(S.spf[X.sp], knot2, dx, dy, dz, put);
+                            inside = orbitals_fast<false>(S.spf[X.sp], knot2, dx, dy, dz, put, ensure_free);
                         }
+                        ensure_free();
+                        // slot rows [nw, 16) must be zero; rows at or above the thread's last nw
+                        // in this buffer already are (each thread owns one (slot, point) column)
+                        const int dirty = b ? a_rows1 : a_rows0;
+                        for (int o = X.nw; o < dirty; ++o)
+                            for (int pc = 0; pc < C::kPieces; ++pc)
+                                *reinterpret_cast<unsigned short*>(A0 + pc * kAPiece + amn(pl, o)) = 0;
+                        if (b) a_rows1 = X.nw; else a_rows0 = X.nw;
                         if (!inside)
                             for (int o = 0; o < X.nw; ++o)
                                 for (int pc = 0; pc < C::kPieces; ++pc)
                                     *reinterpret_cast<unsigned short*>(A0 + pc * kAPiece + amn(pl, o)) = 0;
                     }
+                    ensure_free();
                     tc::fence_async_smem();
                     tc::mbar_arrive(&S.full[b]);
                     uses[b] += 1;
