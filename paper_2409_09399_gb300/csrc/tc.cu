@@ -43,7 +43,6 @@
 
 namespace gint {
 
-constexpr int kTcMaxThreads = 544;   // the larger of the two forms' CTAs (17 warps)
 constexpr int kTcChunk = 16;        // points per K chunk (one MMA K step)
 constexpr int kTcMaxAtoms = 64;     // atom images per brick
 constexpr int kTcMaxSpecies = 8;
@@ -118,7 +117,7 @@ template <bool kExact> struct TcSmem {
     short seg_c0[kTcMaxSeg], seg_c1[kTcMaxSeg], seg_tcol[kTcMaxSeg];
     int pass_first[kTcMaxSeg + 1];      // first segment of each pass
     int npass, nrow, ncol;
-    float wmax[kTcMaxThreads / 32];
+    float wmax[C::kThreads / 32];  // per-warp maxima of |2^s V dV| (every warp of the form's CTA)
     uint64_t full[C::kBufs];   // producers of buffer b arrived (kGroupThreads arrivals)
     uint64_t empty[C::kBufs];  // MMAs reading buffer b completed (tcgen05.commit)
     uint64_t done;      // all MMAs of the pass completed
