@@ -98,6 +98,7 @@ template <bool kExact, int kPW> struct Smem {
     float qd[kMaxCols];                  // exact form: G scale 2^(qa + qD) of each output column of the group
     SpeciesFast spf[kMaxSpecies];
     unsigned char act[kMaxAtoms];
+    unsigned char act_next[kMaxAtoms];  // copy warp: active images of the next M-tile
     uint64_t full[2];    // producers wrote A of buffer b (256 arrivals)
     uint64_t empty[2];   // MMAs reading buffer b completed (tcgen05.commit)
     uint64_t bfull[2];   // bulk copies of B into buffer b completed
@@ -283,6 +284,7 @@ __global__ void __launch_bounds__(RfWarps<kForce, kExact>::kThreads, 1) k_rhofor
     int a_rows0 = 16, a_rows1 = 16;  // producers: rows of their A column in buffer 0 / 1 that may be non-zero
     uint32_t dones = 0;         // completed phases of done
     uint32_t bissue[2] = {0, 0};  // copy warp: bulk-copy phases started per buffer
+    int ahead = 0;                 // copy warp: steps of the coming column group already copied
     uint32_t chunk = 0;  // global chunk counter (buffer parity)
 
     for (;;) {
@@ -348,6 +350,33 @@ __global__ void __launch_bounds__(RfWarps<kForce, kExact>::kThreads, 1) k_rhofor
         __syncthreads();
 
         const int n_mtiles = (g.bpad + 127) / 128;
+        // copy warp: the B copies of one step into buffer bb, K images actK[kk], actK[kk + 1] (nkk
+        // of them) against the column images actN[n0 .. n0 + per_img); lane 0 waits until the
+        // buffer's earlier MMAs and copies are done and opens the transaction phase
+        auto copy_step = [&](int bb, const unsigned char* actK, int kk, int nkk, const unsigned char* actN, int n0,
+                             int per_img) {
+            int go = 0;
+            if (lane == 0) {
+                if (uses[bb] > 0 && !tc::mbar_wait(&S.empty[bb], (uses[bb] - 1) & 1, wait_limit)) atomicOr(&S.abort, 1);
+                // at most one transaction phase of bfull[bb] is ever open: the copies issued
+                // into this buffer before have landed (already true unless a wait gave up)
+                if (bissue[bb] > 0 && !tc::mbar_wait(&S.bfull[bb], (bissue[bb] - 1) & 1, kDrainPolls))
+                    atomicOr(&S.abort, 1);
+                go = S.abort ? 0 : 1;  // after an abort no further copies are started
+                if (go) {
+                    tc::mbar_arrive_expect_tx(&S.bfull[bb], (uint32_t)(nkk * per_img * C::kPieces * kDtPiece));
+                    bissue[bb] += 1;
+                }
+            }
+            go = __shfl_sync(0xffffffffu, go, 0);
+            for (int e = lane; go && e < nkk * per_img; e += 32) {
+                const int jj = e / per_img, sl = e - jj * per_img;
+                const int blk = S.pairblk[actK[kk + jj] * na + actN[n0 + sl]];
+                const unsigned char* src = blk >= 0 ? Dt + (int64_t)blk * kDtBytes : Dzero;
+                tc::bulk_copy_g2s(&S.B[bb][jj][sl * C::kPieces * kDtPiece], src, C::kPieces * kDtPiece, &S.bfull[bb]);
+            }
+            uses[bb] += 1;
+        };
         for (int mt = 0; mt < n_mtiles && !S.abort; ++mt) {
             // ---- active atom images of this M-tile (images within rc of a point of the tile;
             //      tested once per geometry at set-up, k_tile_mask)
@@ -452,34 +481,13 @@ __global__ void __launch_bounds__(RfWarps<kForce, kExact>::kThreads, 1) k_rhofor
                 }
             } else if (warp == kCopyWarp) {
                 // B copies of every step; buffer b is refilled once the MMAs of the step
-                // that last read it have completed (empty[b])
-                for (int st = 0; st < nsteps; ++st) {
-                    const int bb = (chunk + st) & 1, kk = 2 * st;
-                    const int nkk = min(2, nact - kk);
-                    int go = 0;
-                    if (lane == 0) {
-                        if (uses[bb] > 0 && !tc::mbar_wait(&S.empty[bb], (uses[bb] - 1) & 1, wait_limit)) atomicOr(&S.abort, 1);
-                        // at most one transaction phase of bfull[bb] is ever open: the copies issued
-                        // into this buffer before have landed (already true unless a wait gave up)
-                        if (bissue[bb] > 0 && !tc::mbar_wait(&S.bfull[bb], (bissue[bb] - 1) & 1, kDrainPolls))
-                            atomicOr(&S.abort, 1);
-                        go = S.abort ? 0 : 1;  // after an abort no further copies are started
-                        if (go) {
-                            tc::mbar_arrive_expect_tx(&S.bfull[bb], (uint32_t)(nkk * (cg1 - cg0) * C::kPieces * kDtPiece));
-                            bissue[bb] += 1;
-                        }
-                    }
-                    go = __shfl_sync(0xffffffffu, go, 0);
-                    const int per_img = cg1 - cg0;
-                    for (int e = lane; go && e < nkk * per_img; e += 32) {
-                        const int jj = e / per_img, sl = e - jj * per_img;
-                        const int blk = S.pairblk[S.act[kk + jj] * na + S.act[cg0 + sl]];
-                        const unsigned char* src = blk >= 0 ? Dt + (int64_t)blk * kDtBytes : Dzero;
-                        tc::bulk_copy_g2s(&S.B[bb][jj][sl * C::kPieces * kDtPiece], src, C::kPieces * kDtPiece,
-                                          &S.bfull[bb]);
-                    }
-                    uses[bb] += 1;
+                // that last read it have completed (empty[b]).  The first `ahead` steps were
+                // copied during the previous group's epilogue.
+                for (int st = ahead; st < nsteps; ++st) {
+                    const int kk = 2 * st;
+                    copy_step((chunk + st) & 1, S.act, kk, min(2, nact - kk), S.act, cg0, cg1 - cg0);
                 }
+                ahead = 0;
             } else {
                 // MMA issue: one thread waits for A (full) and B (bfull) of each step, issues
                 // its MMAs and commits empty[b]; it never waits for earlier MMAs, so the
@@ -597,6 +605,34 @@ __global__ void __launch_bounds__(RfWarps<kForce, kExact>::kThreads, 1) k_rhofor
                     }
                 }
                 if (warp >= 4 && warp < kProdWarps) S.rho_q[(warp >> 2) - 1][pl] = rho_p;
+                // copy warp of the force kernel, while the others run the epilogue (the force's is
+                // long enough to hide the copies; in rho it made the call slower): both B buffers are
+                // free (every MMA of the group completed); copy the first two steps of the next
+                // column group of the brick (the next group of this M-tile, else the first group of
+                // the next M-tile)
+                if (kForce && warp == kCopyWarp && !S.abort) {
+                    const unsigned char* aK = S.act;
+                    int nK = 0, n0 = 0;
+                    if (cg1 < nact) {
+                        nK = nact;
+                        n0 = cg1;
+                    } else if (mt + 1 < n_mtiles) {
+                        const unsigned long long m = __ldg(P.tile_mask + (int64_t)wl * n_mtiles + mt + 1);
+                        for (int h2 = 0; h2 < 2; ++h2) {
+                            const int a = lane + 32 * h2;
+                            if (m >> a & 1ull) S.act_next[__popcll(m & ((1ull << a) - 1ull))] = (unsigned char)a;
+                        }
+                        __syncwarp();
+                        nK = __popcll(m);
+                        aK = S.act_next;
+                    }
+                    if (nK > 0) {
+                        const int nN = min(nK, n0 + kCols / 16) - n0;
+                        ahead = min(2, (nK + 1) >> 1);
+                        for (int st = 0; st < ahead; ++st)
+                            copy_step((chunk + st) & 1, aK, 2 * st, min(2, nK - 2 * st), aK, n0, nN);
+                    }
+                }
                 tc::fence_before_sync();
                 __syncthreads();
                 if (warp < 4) {
