@@ -2,9 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``.
 
-The local potential that enters Eq. 2 is the sum of the local pseudopotentials,
-the Hartree potential and the exchange-correlation potential (Section 2.2,
-the text after Eq. 2).  This module writes out the two parts that follow from
+V in Eq. 2 has three parts: the atoms' local pseudopotentials, the
+electrostatic (Hartree) potential of rho, and the exchange-correlation
+potential (Section 2.2, the text after Eq. 2).  This module writes out the two parts that follow from
 rho alone, as plain definitions, so that a rho -> V -> H^V loop can be closed
 (the pseudopotential part needs data this work does not have):
 

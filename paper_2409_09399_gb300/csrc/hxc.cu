@@ -1,9 +1,9 @@
 // hxc.cu -- the local potential from rho: Hartree and LDA exchange-correlation parts.
 //
-// The local potential V that enters Eq. 2 is the sum of the local pseudopotentials
-// (an external input here, V_ext), the Hartree potential and the exchange-correlation
-// potential (Section 2.2, the text after Eq. 2; Fig. 1 computes it from rho before the
-// grid integrals).  Here:
+// V in Eq. 2 has three parts: the atoms' local pseudopotentials (an external input here,
+// V_ext), the electrostatic (Hartree) potential of rho and the exchange-correlation
+// potential (Section 2.2, the text after Eq. 2; Fig. 1 forms it from rho before the grid
+// integrals).  Here:
 //   V_H:  the periodic Poisson equation lap V_H = -4 pi (rho - mean rho), solved in
 //         reciprocal space, V_H(G) = 4 pi rho(G) / |G|^2, V_H(G = 0) = 0;
 //   v_xc: LDA, Slater exchange and the Perdew-Zunger (1981) fit of the Ceperley-Alder

@@ -1,8 +1,8 @@
 // tc.cu -- tensor-core (tcgen05) form of the H^V grid integral (Eq. 2).
 //
 // Per brick of grid points the contraction H_b = Psi^T diag(W) Psi (Psi: brick
-// points x brick orbitals, W_p = V_p dV) is a dense small GEMM (Section 2.2:
-// "a batch of points turns vector products into a matrix product").  Here it
+// points x brick orbitals, W_p = V_p dV) is a dense small GEMM (Section 2.2: taking
+// the points in batches turns the per-point products into one matrix product).  Here it
 // runs on the 5th-generation tensor cores:
 //   * orbital rows of the brick are padded to tiles of 128; the upper-triangle
 //     tile pairs (i <= j) accumulate in tensor memory (TMEM, 128 lanes x 512

@@ -2,8 +2,8 @@
 
 The unit of work is the brick (a batch of grid points, Section 2.3.2).  Bricks are dealt to
 ranks as contiguous slabs along the first lattice vector, with slab boundaries placed so that
-every rank gets about the same cost (the paper's "approximately the same number of grid
-computation tasks"; cost per brick from the library's per-brick atom-image counts, so the
+every rank gets about the same cost (Section 2.3.1 gives each process a near-equal share of
+the grid work; cost per brick from the library's per-brick atom-image counts, so the
 slabs adapt to vacuum and to dense regions instead of cutting the cell into equal widths).
 Each rank restricts its handle to its bricks (gint_select_bricks) and computes partial
 results; then
