@@ -79,6 +79,10 @@ template <bool kExact> struct TcCfg {
     static constexpr int kGroupThreads = 32 * kGroupWarps;
     static constexpr int kProdWarps = kGroups * kGroupWarps;
     static constexpr int kThreads = 32 * (kProdWarps + 1);    // + the MMA-issuing warp
+    // A group's chunks use one buffer, so its previous chunk there (whose `empty` wait it
+    // passed) orders the buffer's phases: a wait on the parity of phase u never runs while
+    // the barrier is still in phase u - 2, which a parity wait cannot tell from phase u.
+    static_assert(kGroups == kBufs, "one producer group per operand buffer");
 };
 
 struct TcAtom {
