@@ -92,7 +92,6 @@ template <bool kExact, int kPW> struct Smem {
     int pairblk[kMaxAtoms * kMaxAtoms];  // block (I_a2, I_a1, T_a1 - T_a2) for K image a1, N image a2; -1 if none
     float W2[kMaxBrickPts];              // 2 V dV (force)
     double red[kMaxAtoms][13];           // per-image F(3), virial(9), energy
-    float Gst[kPW][32][17];              // epilogue: G values of one image per lane (padded row)
     float rho_part[128];                 // rho of the tile's points over earlier column groups
     float rho_q[kPW / 4 - 1][128];       // partial rho of warps 4 q .. 4 q + 3, q >= 1
     float qd[kMaxCols];                  // exact form: G scale 2^(qa + qD) of each output column of the group
@@ -108,6 +107,8 @@ template <bool kExact, int kPW> struct Smem {
 };
 
 static_assert(sizeof(Smem<false, 8>) + 1024 <= 232448, "shared memory of the rho/force kernel exceeds 227 KB");
+static_assert(16 * 32 * 17 * sizeof(float) <= sizeof(Smem<true, 16>::A), "epilogue staging exceeds the A buffers");
+static_assert(8 * 32 * 17 * sizeof(float) <= sizeof(Smem<false, 8>::A), "epilogue staging exceeds the A buffers");
 static_assert(sizeof(Smem<true, 16>) + 1024 <= 232448, "shared memory of the exact rho/force kernel exceeds 227 KB");
 
 // Exact form: s = n + l1 + l2 (n = rint(s), |s| <= 128; l1, l2 fp16 pieces of s - n).
@@ -420,6 +421,9 @@ __global__ void __launch_bounds__(RfWarps<kForce, kExact>::kThreads, 1) k_rhofor
             // piece, is exactly the slot's 16-byte rows in the K-major B layout; the copies
             // of step s + 1 start as soon as the MMAs of step s - 1 complete.
             const int nsteps = (nact + 1) >> 1;
+            // the previous group's epilogue staged its G values in the A buffers: no padding row
+            // of A is known to be zero any more
+            a_rows0 = a_rows1 = 16;
             if (warp < kProdWarps) {
                 // group grp fills steps grp, grp + kGroups, ...; the previous use of a step's
                 // buffer is then the group's own previous step (kGroups = 2) or the step before
@@ -561,7 +565,10 @@ __global__ void __launch_bounds__(RfWarps<kForce, kExact>::kThreads, 1) k_rhofor
                     float Gv[16];
                     const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
                     tc::tmem_ld16(ta, Gv);
-                    float* gs = S.Gst[warp][lane];
+                    // G values of the image for this lane (a padded row of 17), staged in the A
+                    // buffers: every MMA of the group has completed, and the next group's
+                    // producers write A only after the epilogue's closing barrier
+                    float* gs = reinterpret_cast<float*>(&S.A[0][0][0]) + (warp * 32 + lane) * 17;
                     if (kExact) {
                         // G = (exact integer part + cross terms) x 2^qa x 2^qD(atom, row)
                         float G1[16];
